@@ -1,0 +1,371 @@
+"""Oracle: Improved Seed-CG in plain FP64 numpy (test infrastructure only).
+
+Every function follows the paper (Abdel-Rehim, Morgan, Wilcox, "Seed methods
+for linear equations in lattice QCD problems with multiple right-hand sides",
+Lattice 2008) in its own order and notation.  `M` is any callable applying the
+Hermitian positive-definite matrix to a flat complex128 vector.
+
+Readings taken where the paper is silent (all listed in the design notes):
+  * alpha_i = Re(v_i^dag f): the imaginary part is roundoff (T is real).
+  * v_2 = f / beta_1 after the first Lanczos iteration (Algorithm 1, step 2
+    never names v_2; step 9 does the same for later i).
+  * Steps 6-7 use v_i before step 8 re-orthogonalises it; the re-orthogonalised
+    v_i is what is stored in V and what step 5 of iteration i+1 uses.  T is
+    not changed by the re-orthogonalisation.
+  * Re-orthogonalisation is classical Gram-Schmidt in the paper's order:
+    v_i against v_1..v_{i-1} then renormalised; f against v_1..v_i.  `po_passes`
+    = 2 repeats each projection once (CGS2).
+  * m_conv is the first i with beta_i |zeta_i / delta_i| <= tol ||b^1||
+    (the D-Lanczos residual norm); the run stops at
+    m = min(m_max, max(m_conv + extra_iters, ceil(past_factor * m_conv))).
+  * Lanczos stops early (m = i) if beta_i <= BREAKDOWN * |alpha_i| (invariant
+    subspace: x^1 is then exact in exact arithmetic).
+  * CG for j >= 2 is textbook Hestenes-Stiefel; convergence is the true
+    residual ||b - M x|| <= tol ||b|| recomputed in FP64.  When the recursive
+    residual says "converged" but the true one does not, CG restarts from the
+    true residual.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+BREAKDOWN = 1e-14
+
+
+def _norm(a: np.ndarray) -> float:
+    return math.sqrt(np.vdot(a, a).real)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (Section 2): Seed-CG(m, k), literal
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LanczosSeedResult:
+    X: np.ndarray                 # [nrhs][N]: x^1 and the seeded guesses x^j (j >= 2)
+    R0: np.ndarray                # [nrhs][N]: r_0^j = b^j - M x_0^j
+    V: np.ndarray                 # [m][N]: stored basis v_1..v_m (after any re-orthogonalisation)
+    alpha: np.ndarray             # [m]
+    beta: np.ndarray              # [m]: beta_1..beta_m
+    beta0: float
+    delta: np.ndarray             # [m]
+    gamma: np.ndarray             # [m-1]: gamma_1..gamma_{m-1}
+    zeta: np.ndarray              # [m]
+    eta: np.ndarray               # [nrhs-1][m]: eta^j after each iteration i
+    resid_est: np.ndarray         # [m]: beta_i |zeta_i / delta_i|
+    m_conv: int
+    m: int
+    po_count: int
+    breakdown: bool = False
+    x1_history: Optional[List[np.ndarray]] = None
+
+
+def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optional[np.ndarray],
+                 tol: float, m_max: int, reorth_period: int, past_factor: float = 1.0,
+                 extra_iters: int = 0, po_passes: int = 1,
+                 keep_x1_history: bool = False) -> LanczosSeedResult:
+    """Algorithm 1, steps 1-9, for the first right-hand side, seeding the others.
+
+    B: [nrhs][N] right-hand sides; X0: initial guesses (None = zero).
+    reorth_period = k (0 = never).  Returns the seeded X and all scalars.
+    """
+    B = np.asarray(B, dtype=np.complex128)
+    nrhs, n = B.shape
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.complex128)
+    # Step 1: initial residuals
+    R0 = np.empty_like(B)
+    for j in range(nrhs):
+        R0[j] = B[j] - M(X[j]) if X0 is not None else B[j].copy()
+    bnorm1 = _norm(B[0])
+
+    V = np.empty((max(m_max, 1), n), dtype=np.complex128)
+    alpha = np.zeros(m_max)
+    beta = np.zeros(m_max)
+    delta = np.zeros(m_max)
+    gamma = np.zeros(max(m_max - 1, 0))
+    zeta = np.zeros(m_max)
+    eta_hist = np.zeros((max(nrhs - 1, 0), m_max), dtype=np.complex128)
+    resid = np.zeros(m_max)
+    hist = [] if keep_x1_history else None
+
+    beta0 = _norm(R0[0])
+    if beta0 == 0.0 or m_max < 1:
+        return LanczosSeedResult(X, R0, V[:0], alpha[:0], beta[:0], beta0, delta[:0], gamma[:0],
+                                 zeta[:0], eta_hist[:, :0], resid[:0], 0, 0, 0, False, hist)
+
+    # Step 2: first Lanczos iteration
+    v = R0[0] / beta0
+    f = M(v)
+    alpha[0] = np.vdot(v, f).real
+    f = f - alpha[0] * v
+    beta[0] = _norm(f)
+    V[0] = v
+    # Step 3: linear equations for the first iteration
+    delta[0] = alpha[0]
+    w = v / delta[0]
+    zeta[0] = beta0
+    X[0] = X[0] + zeta[0] * w
+    # Step 4: other right-hand sides
+    eta = np.zeros(max(nrhs - 1, 0), dtype=np.complex128)
+    for j in range(1, nrhs):
+        eta[j - 1] = np.vdot(v, R0[j])
+        X[j] = X[j] + eta[j - 1] * w
+    eta_hist[:, 0] = eta
+    resid[0] = beta[0] * abs(zeta[0] / delta[0])
+    if hist is not None:
+        hist.append(X[0].copy())
+
+    m = m_max
+    m_conv = 0
+    po_count = 0
+    breakdown = False
+
+    def set_m(i_conv: int) -> int:
+        return min(m_max, max(i_conv + extra_iters, int(math.ceil(past_factor * i_conv))))
+
+    if resid[0] <= tol * bnorm1:
+        m_conv = 1
+        m = set_m(1)
+    if beta[0] <= BREAKDOWN * abs(alpha[0]):
+        breakdown = True
+        m = 1
+    i = 1  # 1-based iteration index of the last completed iteration
+    v_prev = v
+    if m > 1:
+        v = f / beta[0]  # reading: v_2 = f / beta_1
+    while i < m:
+        i += 1
+        k0 = i - 1  # 0-based slot of iteration i
+        # Step 5: Lanczos iteration
+        f = M(v) - beta[k0 - 1] * v_prev
+        alpha[k0] = np.vdot(v, f).real
+        f = f - alpha[k0] * v
+        # Step 6: linear equations
+        g = beta[k0 - 1] / delta[k0 - 1]
+        gamma[k0 - 1] = g
+        delta[k0] = alpha[k0] - g * beta[k0 - 1]
+        w = (v - beta[k0 - 1] * w) / delta[k0]
+        zeta[k0] = -g * zeta[k0 - 1]
+        X[0] = X[0] + zeta[k0] * w
+        # Step 7: other right-hand sides (uses r_0^j, and v_i before step 8)
+        for j in range(1, nrhs):
+            eta[j - 1] = np.vdot(v, R0[j]) - g * eta[j - 1]
+            X[j] = X[j] + eta[j - 1] * w
+        eta_hist[:, k0] = eta
+        # Step 8: periodic re-orthogonalisation
+        if reorth_period > 0 and i % reorth_period == 0:
+            po_count += 1
+            Vp = V[:k0]
+            for _ in range(po_passes):
+                c = Vp.conj() @ v
+                v = v - c @ Vp
+            v = v / _norm(v)
+            Vi = V[:k0 + 1]
+            Vi[k0] = v
+            for _ in range(po_passes):
+                c = Vi.conj() @ f
+                f = f - c @ Vi
+        V[k0] = v
+        # Step 9: finish the iteration
+        beta[k0] = _norm(f)
+        resid[k0] = beta[k0] * abs(zeta[k0] / delta[k0])
+        if hist is not None:
+            hist.append(X[0].copy())
+        if m_conv == 0 and resid[k0] <= tol * bnorm1:
+            m_conv = i
+            m = set_m(i)
+        if beta[k0] <= BREAKDOWN * abs(alpha[k0]):
+            breakdown = True
+            m = i
+            break
+        v_prev = v
+        v = f / beta[k0]
+
+    m = i
+    return LanczosSeedResult(X, R0, V[:m].copy(), alpha[:m].copy(), beta[:m].copy(), beta0,
+                             delta[:m].copy(), gamma[:m - 1].copy(), zeta[:m].copy(),
+                             eta_hist[:, :m].copy(), resid[:m].copy(), m_conv, m, po_count,
+                             breakdown, hist)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (1): the Galerkin seed from the stored basis and T
+# ---------------------------------------------------------------------------
+
+def tridiag(alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
+    """Dense Lanczos T (Eq. 2, left side) of order m from alpha_1..m, beta_1..m-1."""
+    m = len(alpha)
+    t = np.diag(np.asarray(alpha, dtype=np.float64))
+    if m > 1:
+        t += np.diag(beta[:m - 1], 1) + np.diag(beta[:m - 1], -1)
+    return t
+
+
+def galerkin_seed(V: np.ndarray, alpha: np.ndarray, beta: np.ndarray, R0: np.ndarray,
+                  X0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Eq. (1): x^j = x_0^j + V y^j, y^j = T^{-1} (V^dag r_0^j), all j at once."""
+    import scipy.linalg as sla
+    m = V.shape[0]
+    if m == 0:
+        return np.zeros_like(R0) if X0 is None else np.array(X0)
+    rhs = V.conj() @ R0.T                       # [m][nrhs] = V^dag R0
+    ab = np.zeros((3, m), dtype=np.complex128)  # banded storage of T
+    ab[1] = alpha
+    if m > 1:
+        ab[0, 1:] = beta[:m - 1]
+        ab[2, :-1] = beta[:m - 1]
+    Y = sla.solve_banded((1, 1), ab, rhs)
+    X = (V.T @ Y).T
+    return X if X0 is None else X0 + X
+
+
+def lu_factors(alpha: np.ndarray, beta: np.ndarray):
+    """Eq. (2): T = L U with L unit lower bidiagonal (gamma below the
+    diagonal) and U upper bidiagonal (delta on, beta above the diagonal)."""
+    m = len(alpha)
+    delta = np.zeros(m)
+    gamma = np.zeros(max(m - 1, 0))
+    delta[0] = alpha[0]
+    for i in range(1, m):
+        gamma[i - 1] = beta[i - 1] / delta[i - 1]
+        delta[i] = alpha[i] - gamma[i - 1] * beta[i - 1]
+    L = np.eye(m) + np.diag(gamma, -1)
+    U = np.diag(delta) + (np.diag(beta[:m - 1], 1) if m > 1 else 0)
+    return L, U, gamma, delta
+
+
+# ---------------------------------------------------------------------------
+# Standard CG for the seeded systems (Section 2: "a standard CG solver")
+# ---------------------------------------------------------------------------
+
+@dataclass
+class CGResult:
+    x: np.ndarray
+    iters: int
+    true_resid: float      # ||b - M x|| / ||b||
+    converged: bool
+    resid_history: List[float] = field(default_factory=list)
+
+
+def cg(M: Callable[[np.ndarray], np.ndarray], b: np.ndarray, x0: Optional[np.ndarray], tol: float,
+       maxiter: int, keep_history: bool = False, max_restarts: int = 5) -> CGResult:
+    """Hestenes-Stiefel CG; stops on the FP64 true relative residual <= tol."""
+    b = np.asarray(b, dtype=np.complex128)
+    bnorm = _norm(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    if bnorm == 0.0:
+        return CGResult(np.zeros_like(b), 0, 0.0, True, [])
+    hist: List[float] = []
+    it = 0
+    restarts = 0
+    r = b - M(x)
+    while True:
+        rr = np.vdot(r, r).real
+        p = r.copy()
+        if keep_history:
+            hist.append(math.sqrt(rr) / bnorm)
+        while math.sqrt(rr) > tol * bnorm and it < maxiter:
+            q = M(p)
+            a = rr / np.vdot(p, q).real
+            x = x + a * p
+            r = r - a * q
+            rr_new = np.vdot(r, r).real
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+            it += 1
+            if keep_history:
+                hist.append(math.sqrt(rr) / bnorm)
+        r = b - M(x)
+        tr = _norm(r) / bnorm
+        if tr <= tol or it >= maxiter or restarts >= max_restarts:
+            return CGResult(x, it, tr, tr <= tol, hist)
+        restarts += 1
+
+
+# ---------------------------------------------------------------------------
+# The whole method: Algorithm 1 for RHS 1, then CG for the seeded systems
+# ---------------------------------------------------------------------------
+
+@dataclass
+class SolveResult:
+    X: np.ndarray
+    iters: np.ndarray          # per RHS: Lanczos iterations (j=1) + CG iterations
+    true_resid: np.ndarray     # ||b - M x|| / ||b|| per RHS
+    seed: LanczosSeedResult
+    cg_iters: np.ndarray       # CG iterations per RHS (0 for j = 1 unless it needed CG)
+
+
+def improved_seed_cg(M, B, X0, tol, m_max, reorth_period, past_factor=1.0, extra_iters=0,
+                     po_passes=1, seed_mode="literal", cg_maxiter=100000) -> SolveResult:
+    """Seed once with RHS 1 past convergence (Section 2, improvements 1-3),
+    then standard CG for every system whose true residual exceeds tol."""
+    B = np.asarray(B, dtype=np.complex128)
+    nrhs = B.shape[0]
+    res = seed_lanczos(M, B, X0, tol, m_max, reorth_period, past_factor, extra_iters, po_passes)
+    if seed_mode == "blocked":
+        X = galerkin_seed(res.V, res.alpha, res.beta, res.R0,
+                          None if X0 is None else np.asarray(X0, dtype=np.complex128))
+    else:
+        X = res.X.copy()
+    iters = np.zeros(nrhs, dtype=np.int64)
+    cg_iters = np.zeros(nrhs, dtype=np.int64)
+    tr = np.zeros(nrhs)
+    iters[0] = res.m
+    for j in range(nrhs):
+        bn = _norm(B[j])
+        t = _norm(B[j] - M(X[j])) / bn if bn > 0 else 0.0
+        if j == 0 and t <= tol:
+            tr[0] = t
+            continue
+        out = cg(M, B[j], X[j], tol, cg_maxiter)
+        X[j] = out.x
+        cg_iters[j] = out.iters
+        iters[j] += out.iters
+        tr[j] = out.true_resid
+    return SolveResult(X, iters, tr, res, cg_iters)
+
+
+# ---------------------------------------------------------------------------
+# Lanczos estimate of the extreme eigenvalues of M (kappa tuning; set-up only)
+# ---------------------------------------------------------------------------
+
+def lanczos_extremes(M, n: int, seed: int = 12345, max_iters: int = 4000, rtol: float = 2e-3,
+                     check_every: int = 25):
+    """Plain Lanczos from a seeded random start; returns (lam_min, lam_max, iters).
+
+    The extreme Ritz values of T_i converge first and are unaffected by the
+    ghost copies that loss of orthogonality produces; iteration stops when
+    both extremes changed by less than rtol over the last two checks.
+    """
+    import scipy.linalg as sla
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v /= _norm(v)
+    v_prev = np.zeros_like(v)
+    b_prev = 0.0
+    al, be = [], []
+    hist = []
+    for it in range(1, max_iters + 1):
+        f = M(v) - b_prev * v_prev
+        a = np.vdot(v, f).real
+        f -= a * v
+        b = _norm(f)
+        al.append(a)
+        be.append(b)
+        if it % check_every == 0 or b == 0.0 or it == max_iters:
+            ev = sla.eigvalsh_tridiagonal(np.array(al), np.array(be[:-1]))
+            hist.append((ev[0], ev[-1]))
+            if len(hist) >= 3:
+                (l0, h0), (l2, h2) = hist[-3], hist[-1]
+                if abs(l2 - l0) <= rtol * abs(l2) and abs(h2 - h0) <= rtol * abs(h2):
+                    return ev[0], ev[-1], it
+        if b == 0.0:
+            ev = sla.eigvalsh_tridiagonal(np.array(al), np.array(be[:-1]))
+            return ev[0], ev[-1], it
+        v_prev, v = v, f / b
+        b_prev = b
+    return hist[-1][0], hist[-1][1], max_iters

@@ -1,0 +1,221 @@
+"""Pins for the oracle's Improved Seed-CG (CPU only).
+
+Each check ties the oracle to something other than itself: the LU
+factorisation of Eq. (2), textbook CG (the D-Lanczos equivalence the paper
+cites), the closed form of Eq. (1), dense solves and dense eigensolves on tiny
+lattices, and the orthogonality that re-orthogonalisation must restore.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import freefield
+from oracle.seedcg import (cg, galerkin_seed, improved_seed_cg, lanczos_extremes, lu_factors,
+                           seed_lanczos, tridiag)
+from oracle.wilson import WilsonOperator
+from paper_0901_3512_gb300 import workloads as W
+
+DIMS = (4, 2, 2, 4)          # 64 sites, N = 768
+
+
+def _problem(dims=DIMS, kappa=0.2, eps=0.5, seed=7, nrhs=4):
+    op = WilsonOperator(dims, W.gauge_field(dims, eps, seed), kappa)
+    eta = W.z2_sources(dims, nrhs, seed).reshape(nrhs, -1)
+    B = np.stack([op.Ddag(e) for e in eta])
+    return op, eta, B
+
+
+def _textbook_cg_iterates(M, b, n):
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    out = []
+    for _ in range(n):
+        q = M(p)
+        a = rr / np.vdot(p, q).real
+        x = x + a * p
+        r = r - a * q
+        rn = np.vdot(r, r).real
+        p = r + (rn / rr) * p
+        rr = rn
+        out.append(x.copy())
+    return out
+
+
+def test_lu_of_T_reconstructs_T():
+    op, _, B = _problem()
+    res = seed_lanczos(op.M, B, None, 1e-30, 40, 0)
+    T = tridiag(res.alpha, res.beta)
+    L, U, gam, dlt = lu_factors(res.alpha, res.beta)
+    assert np.abs(L @ U - T).max() <= 1e-14 * np.abs(T).max()
+    # the recurrence inside Algorithm 1 (step 6) gives the same factors
+    assert np.allclose(res.delta, dlt, rtol=1e-13, atol=0)
+    assert np.allclose(res.gamma, gam, rtol=1e-13, atol=0)
+    # tridiagonal solve by the factors equals a dense solve
+    rhs = np.arange(1.0, len(res.alpha) + 1)
+    y = np.linalg.solve(U, np.linalg.solve(L, rhs))
+    assert np.allclose(y, np.linalg.solve(T, rhs), rtol=1e-9)
+
+
+def test_lanczos_first_rhs_equals_textbook_cg():
+    """D-Lanczos is CG: x^1 after i steps equals the i-th CG iterate, and
+    beta_i |zeta_i/delta_i| equals the true residual norm."""
+    op, _, B = _problem()
+    n = 20
+    res = seed_lanczos(op.M, B[:1], None, 1e-30, n, 0, keep_x1_history=True)
+    ref = _textbook_cg_iterates(op.M, B[0], n)
+    for i in range(n):
+        x = res.x1_history[i]
+        assert np.linalg.norm(x - ref[i]) <= 1e-10 * np.linalg.norm(ref[i])
+        true_r = np.linalg.norm(B[0] - op.M(x))
+        assert abs(res.resid_est[i] - true_r) <= 1e-8 * np.linalg.norm(B[0])
+
+
+def test_literal_seed_equals_eq1():
+    """Steps 4 and 7 (incremental LU update) reproduce x_0 + V T^{-1} V^dag r_0."""
+    op, _, B = _problem()
+    rng = np.random.default_rng(3)
+    X0 = 0.01 * (rng.standard_normal(B.shape) + 1j * rng.standard_normal(B.shape))
+    res = seed_lanczos(op.M, B, X0, 1e-30, 30, 0)
+    Xb = galerkin_seed(res.V, res.alpha, res.beta, res.R0, X0)
+    # dense T^{-1} as a second route to Eq. (1)
+    T = tridiag(res.alpha, res.beta)
+    Xd = X0 + (res.V.T @ np.linalg.solve(T, res.V.conj() @ res.R0.T)).T
+    for j in range(B.shape[0]):
+        nrm = np.linalg.norm(Xd[j])
+        assert np.linalg.norm(res.X[j] - Xd[j]) <= 1e-10 * nrm
+        assert np.linalg.norm(Xb[j] - Xd[j]) <= 1e-12 * nrm
+    # R0 really is b - M x0
+    assert np.linalg.norm(res.R0[1] - (B[1] - op.M(X0[1]))) < 1e-14 * np.linalg.norm(B[1])
+
+
+def test_galerkin_condition_with_po():
+    """x^j from Eq. (1) makes the residual orthogonal to span(V)."""
+    op, _, B = _problem()
+    res = seed_lanczos(op.M, B, None, 1e-30, 60, 1)
+    X = galerkin_seed(res.V, res.alpha, res.beta, res.R0)
+    for j in range(1, B.shape[0]):
+        g = res.V.conj() @ (B[j] - op.M(X[j]))
+        assert np.linalg.norm(g) <= 1e-8 * np.linalg.norm(res.V.conj() @ res.R0[j])
+
+
+def test_periodic_reorthogonalisation_restores_orthogonality():
+    """Plain Lanczos loses orthogonality once Ritz values converge (Section 2);
+    PO every k steps keeps V orthonormal to ~1e-10 right after each PO step."""
+    op, _, B = _problem(kappa=0.22)
+    m = 200
+    plain = seed_lanczos(op.M, B[:1], None, 1e-30, m, 0)
+    loss = np.abs(plain.V.conj() @ plain.V.T - np.eye(plain.m)).max()
+    assert loss > 1e-4
+    k = 10
+    po = seed_lanczos(op.M, B[:1], None, 1e-30, m, k)
+    assert po.po_count == m // k
+    for i in range(k, po.m + 1, k):
+        Vi = po.V[:i]
+        assert np.abs(Vi.conj() @ Vi.T - np.eye(i)).max() <= 1e-10
+    full = seed_lanczos(op.M, B[:1], None, 1e-30, m, 1, po_passes=2)
+    assert np.abs(full.V.conj() @ full.V.T - np.eye(full.m)).max() <= 1e-12
+
+
+def test_T_extreme_ritz_values_match_dense_spectrum():
+    """Past convergence, T_m holds the extreme eigenvalues of M (Section 2:
+    the subspace contains accurate low eigenvectors)."""
+    dims = (4, 4, 4, 4)
+    op = WilsonOperator(dims, W.gauge_field(dims, 0.3, 0), 0.2)
+    ev = np.linalg.eigvalsh(op.dense(WilsonOperator.OP_M))
+    b = op.Ddag(W.z2_sources(dims, 1, 0).reshape(-1))
+    res = seed_lanczos(op.M, b[None], None, 1e-10, 600, 10, past_factor=2.0)
+    assert res.m_conv > 0 and res.m >= 2 * res.m_conv - 1
+    ritz = np.linalg.eigvalsh(tridiag(res.alpha, res.beta))
+    assert abs(ritz[0] - ev[0]) <= 1e-8 * ev[0]
+    assert abs(ritz[-1] - ev[-1]) <= 1e-8 * ev[-1]
+
+
+@pytest.mark.parametrize("seed_mode", ["literal", "blocked"])
+def test_whole_method_against_dense_solve(seed_mode):
+    op, _, B = _problem(nrhs=5)
+    Md = op.dense(WilsonOperator.OP_M)
+    ev = np.linalg.eigvalsh(Md)
+    cond = ev[-1] / ev[0]
+    tol = 1e-8
+    out = improved_seed_cg(op.M, B, None, tol, 2000, 10, past_factor=1.5, seed_mode=seed_mode)
+    Xd = np.linalg.solve(Md, B.T).T
+    for j in range(B.shape[0]):
+        assert out.true_resid[j] <= tol
+        assert np.linalg.norm(B[j] - Md @ out.X[j]) <= tol * np.linalg.norm(B[j])
+        assert np.linalg.norm(out.X[j] - Xd[j]) <= cond * tol * np.linalg.norm(Xd[j])
+    # seeding pays: the seeded systems need fewer CG iterations than from zero
+    plain = [cg(op.M, B[j], None, tol, 5000).iters for j in range(1, B.shape[0])]
+    assert max(out.cg_iters[1:]) < min(plain)
+
+
+def test_brute_force_2x2x2x2():
+    dims = (2, 2, 2, 2)
+    op = WilsonOperator(dims, W.gauge_field(dims, 0.8, 5), 0.19)
+    B = W.random_spinors(dims, 3, 1).reshape(3, -1)
+    d = op.dense(WilsonOperator.OP_D)
+    Md = d.conj().T @ d
+    out = improved_seed_cg(op.M, B, None, 1e-10, 500, 5, past_factor=2.0)
+    Xd = np.linalg.solve(Md, B.T).T
+    cond = np.linalg.cond(Md)
+    for j in range(3):
+        assert np.linalg.norm(out.X[j] - Xd[j]) <= cond * 1e-10 * np.linalg.norm(Xd[j])
+
+
+def test_m_rule_past_convergence_and_extra_iters():
+    op, _, B = _problem(nrhs=2)
+    a = seed_lanczos(op.M, B, None, 1e-8, 5000, 10, past_factor=1.5)
+    assert a.m == math.ceil(1.5 * a.m_conv)
+    b = seed_lanczos(op.M, B, None, 1e-8, 5000, 10, past_factor=1.0, extra_iters=7)
+    assert b.m_conv == a.m_conv and b.m == a.m_conv + 7
+    c = seed_lanczos(op.M, B, None, 1e-8, a.m_conv + 3, 10, past_factor=2.0)
+    assert c.m == a.m_conv + 3
+    # m_conv is the first i whose residual estimate is below tol ||b^1||
+    bn = np.linalg.norm(B[0])
+    assert a.resid_est[a.m_conv - 1] <= 1e-8 * bn < a.resid_est[a.m_conv - 2]
+
+
+def test_edge_cases():
+    op, _, B = _problem(nrhs=3)
+    # zero first right-hand side: no Lanczos, others go straight to CG
+    Bz = B.copy()
+    Bz[0] = 0
+    out = improved_seed_cg(op.M, Bz, None, 1e-8, 100, 10)
+    assert out.seed.m == 0 and np.all(out.X[0] == 0)
+    assert out.true_resid[1] <= 1e-8 and out.true_resid[2] <= 1e-8
+    # one right-hand side
+    out1 = improved_seed_cg(op.M, B[:1], None, 1e-8, 2000, 10, past_factor=1.0)
+    assert out1.true_resid[0] <= 1e-8
+    # exact initial guess for RHS 1
+    x_exact = np.linalg.solve(op.dense(WilsonOperator.OP_M), B[0])
+    X0 = np.zeros_like(B)
+    X0[0] = x_exact
+    res = seed_lanczos(op.M, B, X0, 1e-8, 100, 10)
+    assert res.beta0 <= 1e-10 * np.linalg.norm(B[0])
+
+
+def test_breakdown_on_eigenvector():
+    """b^1 an eigenvector of M: beta_1 = 0, x^1 = b/lambda is exact at i = 1."""
+    dims = (4, 2, 2, 4)
+    op = WilsonOperator(dims, W.unit_gauge(dims), 0.1)
+    p = (np.pi / 2, 0.0, np.pi, np.pi / 4)
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal((4, 3)) + 0j
+    b = freefield.plane_wave(dims, p, u).reshape(-1)
+    res = seed_lanczos(op.M, b[None], None, 1e-8, 50, 10)
+    assert res.breakdown and res.m == 1
+    lam = (1 - 2 * 0.1 * sum(np.cos(q) for q in p)) ** 2 + 4 * 0.01 * sum(np.sin(q) ** 2 for q in p)
+    assert np.linalg.norm(res.X[0] - b / lam) <= 1e-13 * np.linalg.norm(b / lam)
+
+
+def test_lanczos_extremes_free_field_cond():
+    """Set-up pin: the tuning's Lanczos cond estimate equals the closed form."""
+    dims = (8, 8, 4, 8)
+    kappa = 0.124
+    op = WilsonOperator(dims, W.unit_gauge(dims), kappa)
+    lo, hi, _ = lanczos_extremes(op.M, op.n, max_iters=3000, rtol=1e-6)
+    ev = freefield.spectrum_M(dims, kappa)
+    assert abs(lo - ev[0]) <= 1e-4 * ev[0]
+    assert abs(hi - ev[-1]) <= 1e-6 * ev[-1]
