@@ -159,16 +159,7 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
         # Step 8: periodic re-orthogonalisation
         if reorth_period > 0 and i % reorth_period == 0:
             po_count += 1
-            Vp = V[:k0]
-            for _ in range(po_passes):
-                c = Vp.conj() @ v
-                v = v - c @ Vp
-            v = v / _norm(v)
-            Vi = V[:k0 + 1]
-            Vi[k0] = v
-            for _ in range(po_passes):
-                c = Vi.conj() @ f
-                f = f - c @ Vi
+            v, f = periodic_reorth(V, i, v, f, po_passes)
         V[k0] = v
         # Step 9: finish the iteration
         beta[k0] = _norm(f)
@@ -190,6 +181,24 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
                              delta[:m].copy(), gamma[:m - 1].copy(), zeta[:m].copy(),
                              eta_hist[:, :m].copy(), resid[:m].copy(), m_conv, m, po_count,
                              breakdown, hist)
+
+
+def periodic_reorth(V: np.ndarray, i: int, v: np.ndarray, f: np.ndarray, passes: int = 1):
+    """Step 8 of Algorithm 1 at iteration i (1-based), classical Gram-Schmidt.
+
+    V holds v_1..v_{i-1} in rows 0..i-2.  Re-orthonormalise v_i against
+    v_1..v_{i-1}; then re-orthogonalise f (the un-normalised v_{i+1}) against
+    v_1..v_i, v_i being the new one.  Row i-1 of V receives the new v_i.
+    """
+    prev = V[:i - 1]
+    for _ in range(passes):
+        v = v - (prev.conj() @ v) @ prev
+    v = v / _norm(v)
+    V[i - 1] = v
+    upto = V[:i]
+    for _ in range(passes):
+        f = f - (upto.conj() @ f) @ upto
+    return v, f
 
 
 # ---------------------------------------------------------------------------

@@ -219,3 +219,27 @@ def test_lanczos_extremes_free_field_cond():
     ev = freefield.spectrum_M(dims, kappa)
     assert abs(lo - ev[0]) <= 1e-4 * ev[0]
     assert abs(hi - ev[-1]) <= 1e-6 * ev[-1]
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_step8_reorth_against_every_previous_vector(passes):
+    """Step 8 in isolation: v_i leaves orthogonal to ALL of v_1..v_{i-1} (even
+    when it leans on v_{i-1}), with unit norm and in span(V, v_i); f leaves
+    orthogonal to v_1..v_i."""
+    rng = np.random.default_rng(4)
+    n, i = 300, 9
+    q, _ = np.linalg.qr(rng.standard_normal((n, i - 1)) + 1j * rng.standard_normal((n, i - 1)))
+    V = np.zeros((i + 2, n), dtype=np.complex128)
+    V[:i - 1] = q.T
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = 0.1 * z + 3.0 * V[i - 2] + 0.5 * V[0]
+    f = rng.standard_normal(n) + 1j * rng.standard_normal(n) + 2.0 * V[i - 2]
+    from oracle.seedcg import periodic_reorth
+    v2, f2 = periodic_reorth(V, i, v, f, passes)
+    assert abs(np.linalg.norm(v2) - 1) < 1e-14
+    assert np.abs(V[:i - 1].conj() @ v2).max() < 1e-14
+    assert np.abs(V[:i].conj() @ f2).max() < 1e-13
+    assert np.array_equal(V[i - 1], v2)
+    # v2 is (z's part outside span V_{i-1}) normalised: the only admissible result
+    zp = z - (V[:i - 1].conj() @ z) @ V[:i - 1]
+    assert np.linalg.norm(v2 - zp / np.linalg.norm(zp)) < 1e-13
