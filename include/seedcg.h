@@ -1,0 +1,162 @@
+/*
+ * seedcg.h - C ABI of the GB300 (sm_103a) Improved Seed-CG library.
+ *
+ * The library solves many Hermitian positive-definite systems
+ *     M x^j = b^j,  j = 1..nrhs,   M = D^dag D,   D = 1 - kappa H_Wilson
+ * with the Improved Seed-CG method of Abdel-Rehim, Morgan and Wilcox
+ * ("Seed methods for linear equations in lattice QCD problems with multiple
+ * right-hand sides", Lattice 2008): the first system is solved by Lanczos
+ * (Algorithm 1) past convergence with periodic re-orthogonalisation (PO),
+ * its stored basis V seeds every other system through the Galerkin
+ * projection of Eq. (1) updated with the LU factorisation of T (Eq. 2), and
+ * standard CG finishes the seeded systems (Section 2).
+ *
+ * Conventions shared by every call (Section 3 names the operator only as
+ * "Wilson fermions"; these are the conventions this library fixes):
+ *   - site index s = x + Lx*(y + Ly*(z + Lz*t)); mu = 0,1,2,3 <-> x,y,z,t.
+ *   - gauge field: complex128 (re, im interleaved doubles) [site][mu][a][b],
+ *     U_mu(x) with colour row a, column b.
+ *   - spinor field: complex128 [site][spin 4][colour 3]; a batch of n spinor
+ *     fields is n such fields back to back.
+ *   - (D psi)(x) = psi(x) - kappa sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                         + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ *     periodic in x,y,z and antiperiodic in t (a factor -1 on hops that wrap
+ *     t); chiral gamma basis g_k = [[0,-i s_k],[i s_k,0]], g_4 = [[0,1],[1,0]];
+ *     D^dag = g5 D g5, g5 = diag(1,1,-1,-1).
+ *
+ * Memory: a pointer argument documented as "host or device" may be either;
+ * the library asks the CUDA runtime which one it is.  Device pointers must
+ * be on the device that was current at seedcg_create.  All device work is
+ * ordered on the caller's stream (NULL = legacy default stream); every call
+ * returns after that work has completed unless documented otherwise.
+ *
+ * Errors: every call returns a seedcg_status.  Arguments are checked before
+ * any device work; on failure seedcg_last_error() describes it.  No call
+ * throws across the ABI.  A handle is not thread-safe: one caller at a time.
+ */
+#ifndef SEEDCG_H
+#define SEEDCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct seedcg_handle seedcg_handle;
+
+typedef enum {
+    SEEDCG_OK = 0,
+    SEEDCG_ERR_ARG = -1,            /* invalid argument (nothing was run)          */
+    SEEDCG_ERR_OOM = -2,            /* device allocation failed                    */
+    SEEDCG_ERR_CUDA = -3,           /* a CUDA runtime call failed                  */
+    SEEDCG_ERR_NOT_CONVERGED = -4,  /* an iteration limit was hit; X = best iterate */
+    SEEDCG_ERR_BREAKDOWN = -5,      /* delta_i = 0 in the LU of T (M not HPD)      */
+    SEEDCG_ERR_NAN = -6,            /* a NaN/Inf appeared in a scalar              */
+    SEEDCG_ERR_TIMEOUT = -7         /* a bounded device wait ran out               */
+} seedcg_status;
+
+typedef enum {
+    SEEDCG_FP64 = 0,          /* every vector, V and the dslash in FP64                  */
+    SEEDCG_MIXED_V32 = 1,     /* FP32 dslash and vectors, V in complex64, FP64 scalars    */
+    SEEDCG_MIXED_VBF16 = 2    /* as MIXED_V32 but V stored in bf16 (tensor-core projections) */
+} seedcg_precision;
+
+typedef struct {
+    int m_max;             /* largest Krylov dimension m stored in V (Algorithm 1, "m");
+                              0 = default 4000 */
+    double past_factor;    /* >= 1: run RHS 1 to m = max(m_conv + extra_iters,
+                              ceil(past_factor * m_conv)), capped by m_max (Section 2:
+                              "solved past the convergence limit")                  */
+    int precision;         /* seedcg_precision                                          */
+    double reliable_delta; /* mixed CG: recompute the FP64 true residual whenever the
+                              iterated residual fell by this factor (default 0.1)      */
+    int po_passes;         /* 1 = classical Gram-Schmidt, 2 = CGS2 (default 1)         */
+    int seed_mode;         /* 0 = literal per-iteration updates (Algorithm 1 steps 3-7;
+                              FP64 only), 1 = blocked Eq. (1) after the Lanczos run    */
+    int x0_given;          /* 1: X holds initial guesses x_0^j on entry                */
+    int cg_maxiter;        /* CG iteration cap per system (default 20000)               */
+    int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */
+    int poll_every;        /* iterations between host polls of device flags (default 32) */
+} seedcg_options;
+
+typedef struct {
+    /* filled by seedcg_solve; the array pointers are caller-owned host arrays
+       of nrhs entries each, or NULL to skip them */
+    int m_conv;            /* first i with beta_i |zeta_i/delta_i| <= tol ||b^1||        */
+    int m;                 /* Lanczos iterations run (basis size)                       */
+    int po_count;          /* periodic re-orthogonalisation steps taken                 */
+    int cg_iters_max;      /* CG iterations of the slowest seeded system                */
+    int reliable_updates;  /* FP64 residual recomputations in the CG phase              */
+    int* iters;            /* per RHS: Lanczos iterations (j=1) + CG iterations         */
+    int* matvecs;          /* per RHS: applications of D or D^dag                        */
+    double* true_resid;    /* per RHS: ||b - M x|| / ||b||, FP64                         */
+    float ms_total, ms_lanczos, ms_po, ms_seed, ms_cg;   /* device-event phase times    */
+} seedcg_info;
+
+/* Fill *opt with the defaults documented above. */
+void seedcg_default_options(seedcg_options* opt);
+
+/*
+ * Create a solver for one gauge field (Section 3: one configuration, many
+ * right-hand sides).  dims = {Lx, Ly, Lz, Lt}, each >= 2 and even.
+ * gauge: host or device, complex128 [V][4][3][3]; copied, the caller keeps
+ * ownership.  kappa: hopping parameter.  opt may be NULL (defaults).
+ * Returns SEEDCG_ERR_ARG for bad dims/pointers, SEEDCG_ERR_OOM/CUDA on
+ * device failures; *h is NULL on failure.
+ */
+seedcg_status seedcg_create(seedcg_handle** h, const int dims[4], const double* gauge,
+                            double kappa, const seedcg_options* opt);
+
+/* Change options of an existing handle (takes effect at the next solve). */
+seedcg_status seedcg_set_options(seedcg_handle* h, const seedcg_options* opt);
+
+/*
+ * Solve M x^j = b^j for j = 1..nrhs (Section 2, Algorithm 1 + CG).
+ * B: host or device, complex128 [nrhs][V][4][3], read only.
+ * X: host or device, same layout; on entry x_0^j if opt.x0_given, on exit the
+ *    solutions (or the seeded guesses if opt.stop_after_seed).
+ * tol: relative residual; convergence is ||b - M x|| <= tol ||b|| in FP64.
+ * extra_iters: Lanczos iterations past m_conv (see seedcg_options.past_factor).
+ * reorth_period: k of Algorithm 1 (PO every k iterations), 0 = none.
+ * info: NULL or filled on return (also on NOT_CONVERGED).
+ * stream: cudaStream_t or NULL.
+ */
+seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
+                           int extra_iters, int reorth_period, seedcg_info* info,
+                           void* stream);
+
+/*
+ * Apply the operator to n spinor fields (for parity checks and for forming
+ * b = D^dag eta).  op: 0 = D, 1 = D^dag, 2 = M = D^dag D.  prec: 0 = FP64
+ * arithmetic, 1 = FP32 arithmetic (inputs rounded to FP32, result widened).
+ * in/out: device pointers, complex128 [n][V][4][3]; they may not overlap.
+ * multi = 1 uses the multi-RHS kernel (links staged once per site tile for
+ * all n fields), 0 the single-RHS kernel n times.
+ */
+seedcg_status seedcg_apply(seedcg_handle* h, int op, int prec, int multi, int n,
+                           const double* in, double* out, void* stream);
+
+/*
+ * After a solve: copy the Lanczos scalars of RHS 1 (alpha_1..m, beta_1..m,
+ * delta_1..m; Eq. 2) into caller host arrays of `cap` doubles (any may be
+ * NULL).  Returns the number m written via *m_out.
+ */
+seedcg_status seedcg_get_lanczos(const seedcg_handle* h, int cap, double* alpha, double* beta,
+                                 double* delta, int* m_out);
+
+/*
+ * After a solve: copy stored basis vectors v_first .. v_first+count-1 (0-based)
+ * as complex128 [count][V][4][3] into `out` (host or device).  Works for every
+ * V precision (the stored values are widened).
+ */
+seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* out);
+
+/* Message for the last failing call on h (never NULL). */
+const char* seedcg_last_error(const seedcg_handle* h);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void seedcg_destroy(seedcg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEEDCG_H */

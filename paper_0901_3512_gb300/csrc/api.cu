@@ -1,0 +1,297 @@
+// The C ABI (include/seedcg.h): argument checks, host/device staging, and
+// the dispatch to the solver and the dslash kernels.  No exception crosses
+// the ABI: every entry point converts failures into a seedcg_status and a
+// message kept in the handle.
+#include <cstring>
+#include <new>
+
+#include "handle.cuh"
+#include "kernels.cuh"
+
+using seedcg::Error;
+
+namespace {
+
+constexpr size_t kPinnedBytes = 64 * 1024;
+
+thread_local std::string g_create_error;
+
+seedcg_status fail(seedcg_handle* h, seedcg_status code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool valid_options(const seedcg_options& o, std::string& why) {
+    if (o.m_max < 1) { why = "m_max must be >= 1"; return false; }
+    if (!(o.past_factor >= 1.0)) { why = "past_factor must be >= 1"; return false; }
+    if (o.precision < 0 || o.precision > 2) { why = "unknown precision mode"; return false; }
+    if (!(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)) { why = "reliable_delta must be in (0,1)"; return false; }
+    if (o.po_passes < 1 || o.po_passes > 2) { why = "po_passes must be 1 or 2"; return false; }
+    if (o.seed_mode < 0 || o.seed_mode > 1) { why = "seed_mode must be 0 or 1"; return false; }
+    if (o.seed_mode == 0 && o.precision != SEEDCG_FP64) { why = "literal seeding (seed_mode 0) needs precision FP64"; return false; }
+    if (o.cg_maxiter < 1) { why = "cg_maxiter must be >= 1"; return false; }
+    if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void seedcg_default_options(seedcg_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->m_max = 4000;
+    opt->past_factor = 1.0;
+    opt->precision = SEEDCG_FP64;
+    opt->reliable_delta = 0.1;
+    opt->po_passes = 1;
+    opt->seed_mode = 1;
+    opt->x0_given = 0;
+    opt->cg_maxiter = 20000;
+    opt->stop_after_seed = 0;
+    opt->poll_every = 32;
+}
+
+seedcg_status seedcg_create(seedcg_handle** out, const int dims[4], const double* gauge,
+                            double kappa, const seedcg_options* opt) {
+    if (!out) return fail(nullptr, SEEDCG_ERR_ARG, "h is NULL");
+    *out = nullptr;
+    if (!dims || !gauge) return fail(nullptr, SEEDCG_ERR_ARG, "dims or gauge is NULL");
+    long vol = 1;
+    for (int i = 0; i < 4; i++) {
+        if (dims[i] < 2 || (dims[i] & 1))
+            return fail(nullptr, SEEDCG_ERR_ARG, "every lattice extent must be even and >= 2");
+        vol *= dims[i];
+    }
+    if (vol * 12 > (1L << 31) - 1) return fail(nullptr, SEEDCG_ERR_ARG, "lattice too large");
+    if (!(kappa == kappa)) return fail(nullptr, SEEDCG_ERR_ARG, "kappa is NaN");
+    seedcg_options o;
+    seedcg_default_options(&o);
+    if (opt) o = *opt;
+    std::string why;
+    if (!valid_options(o, why)) return fail(nullptr, SEEDCG_ERR_ARG, why);
+    seedcg_handle* h = new (std::nothrow) seedcg_handle();
+    if (!h) return fail(nullptr, SEEDCG_ERR_OOM, "host allocation failed");
+    try {
+        h->g = seedcg::make_geom(dims);
+        h->kappa = kappa;
+        h->opt = o;
+        SEEDCG_CUDA_TRY(cudaGetDevice(&h->device));
+        SEEDCG_CUDA_TRY(cudaMallocHost(&h->pinned, kPinnedBytes));
+        const size_t nl = (size_t)vol * 36;
+        h->u64.ensure(nl * sizeof(double2));
+        h->u32.ensure(nl * sizeof(float2));
+        const double* src = gauge;
+        seedcg::DevBuf tmp;
+        if (!is_device_ptr(gauge)) {
+            tmp.ensure(nl * sizeof(double2));
+            SEEDCG_CUDA_TRY(cudaMemcpy(tmp.p, gauge, nl * sizeof(double2), cudaMemcpyHostToDevice));
+            src = tmp.as<double>();
+        }
+        seedcg::gauge_to_internal(src, h->u64.as<double2>(), h->u32.as<float2>(), (int)vol, 0);
+        SEEDCG_CUDA_TRY(cudaDeviceSynchronize());
+        tmp.release();
+    } catch (const Error& e) {
+        g_create_error = e.msg;
+        seedcg_destroy(h);
+        return e.code;
+    }
+    *out = h;
+    return SEEDCG_OK;
+}
+
+seedcg_status seedcg_set_options(seedcg_handle* h, const seedcg_options* opt) {
+    if (!h || !opt) return fail(h, SEEDCG_ERR_ARG, "h or opt is NULL");
+    std::string why;
+    if (!valid_options(*opt, why)) return fail(h, SEEDCG_ERR_ARG, why);
+    h->opt = *opt;
+    return SEEDCG_OK;
+}
+
+seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
+                           int extra_iters, int reorth_period, seedcg_info* info, void* stream) {
+    if (!h) return fail(nullptr, SEEDCG_ERR_ARG, "h is NULL");
+    if (nrhs < 1 || nrhs > 256) return fail(h, SEEDCG_ERR_ARG, "nrhs must be in [1, 256]");
+    if (!B || !X) return fail(h, SEEDCG_ERR_ARG, "B or X is NULL");
+    if (!(tol > 0.0) || !(tol < 1.0)) return fail(h, SEEDCG_ERR_ARG, "tol must be in (0, 1)");
+    if (extra_iters < 0 || reorth_period < 0)
+        return fail(h, SEEDCG_ERR_ARG, "extra_iters and reorth_period must be >= 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        const size_t bytes = (size_t)nrhs * h->g.vol * 12 * sizeof(double2);
+        const bool bd = is_device_ptr(B), xd = is_device_ptr(X);
+        seedcg::DevBuf hb, hx;
+        const double* Bd = B;
+        double* Xd = X;
+        if (!bd) {
+            hb.ensure(bytes);
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hb.p, B, bytes, cudaMemcpyHostToDevice, st));
+            Bd = hb.as<double>();
+        }
+        if (!xd) {
+            hx.ensure(bytes);
+            if (h->opt.x0_given)
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(hx.p, X, bytes, cudaMemcpyHostToDevice, st));
+            Xd = hx.as<double>();
+        }
+        seedcg_status code = seedcg::solve_impl(h, nrhs, Bd, Xd, tol, extra_iters, reorth_period,
+                                                info, st);
+        if (!xd) {
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(X, Xd, bytes, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        if (code != SEEDCG_OK) {
+            const char* what = code == SEEDCG_ERR_NOT_CONVERGED ? "a system did not converge"
+                             : code == SEEDCG_ERR_BREAKDOWN ? "delta_i = 0 in the LU of T (M not HPD?)"
+                             : code == SEEDCG_ERR_NAN ? "NaN/Inf in a Lanczos scalar"
+                             : "solve failed";
+            h->err = what;
+        }
+        return code;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_apply(seedcg_handle* h, int op, int prec, int multi, int n, const double* in,
+                           double* out, void* stream) {
+    if (!h) return fail(nullptr, SEEDCG_ERR_ARG, "h is NULL");
+    if (op < 0 || op > 2 || prec < 0 || prec > 1 || n < 0)
+        return fail(h, SEEDCG_ERR_ARG, "bad op/prec/n");
+    if (n == 0) return SEEDCG_OK;
+    if (!in || !out || in == out) return fail(h, SEEDCG_ERR_ARG, "in/out NULL or aliased");
+    if (!is_device_ptr(in) || !is_device_ptr(out))
+        return fail(h, SEEDCG_ERR_ARG, "seedcg_apply takes device pointers");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        const int vol = h->g.vol;
+        const size_t nf = (size_t)n * vol * 12;
+        const size_t esz = prec == 0 ? sizeof(double2) : sizeof(float2);
+        seedcg::DevBuf buf;
+        buf.ensure(3 * nf * esz + 512);
+        char* b0 = buf.as<char>();
+        void* A = b0;
+        void* Bv = b0 + nf * esz;
+        void* Cv = b0 + 2 * nf * esz;
+        if (prec == 0) {
+            seedcg::to_internal_f64(in, (double2*)A, vol, n, st);
+            auto apply = [&](int dag, const double2* x, double2* y) {
+                if (multi) seedcg::dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, dag, n, x, y, st);
+                else
+                    for (int r = 0; r < n; r++)
+                        seedcg::dslash_f64(h->g, h->u64.as<double2>(), h->kappa, dag,
+                                           x + (size_t)r * 12 * vol, y + (size_t)r * 12 * vol, st);
+            };
+            const double2* res = nullptr;
+            if (op == 0) { apply(0, (double2*)A, (double2*)Bv); res = (double2*)Bv; }
+            else if (op == 1) { apply(1, (double2*)A, (double2*)Bv); res = (double2*)Bv; }
+            else { apply(0, (double2*)A, (double2*)Bv); apply(1, (double2*)Bv, (double2*)Cv); res = (double2*)Cv; }
+            seedcg::from_internal_f64(res, out, vol, n, st);
+        } else {
+            seedcg::to_internal_f32(in, (float2*)A, vol, n, st);
+            const float k = (float)h->kappa;
+            auto apply = [&](int dag, const float2* x, float2* y) {
+                if (multi) seedcg::dslash_mrhs_f32(h->g, h->u32.as<float2>(), k, dag, n, x, y, st);
+                else
+                    for (int r = 0; r < n; r++)
+                        seedcg::dslash_f32(h->g, h->u32.as<float2>(), k, dag,
+                                           x + (size_t)r * 12 * vol, y + (size_t)r * 12 * vol, st);
+            };
+            const float2* res = nullptr;
+            if (op == 0) { apply(0, (float2*)A, (float2*)Bv); res = (float2*)Bv; }
+            else if (op == 1) { apply(1, (float2*)A, (float2*)Bv); res = (float2*)Bv; }
+            else { apply(0, (float2*)A, (float2*)Bv); apply(1, (float2*)Bv, (float2*)Cv); res = (float2*)Cv; }
+            seedcg::from_internal_f32(res, out, vol, n, st);
+        }
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_get_lanczos(const seedcg_handle* h, int cap, double* alpha, double* beta,
+                                 double* delta, int* m_out) {
+    if (!h) return SEEDCG_ERR_ARG;
+    const int m = h->last_m;
+    if (m_out) *m_out = m;
+    const int c = cap < m ? cap : m;
+    for (int i = 0; i < c; i++) {
+        if (alpha) alpha[i] = h->alpha[i];
+        if (beta) beta[i] = h->beta[i];
+        if (delta) delta[i] = h->delta[i];
+    }
+    return SEEDCG_OK;
+}
+
+seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* out) {
+    if (!h || !out) return fail(h, SEEDCG_ERR_ARG, "h or out is NULL");
+    if (first < 0 || count < 0 || first + count > h->vbasis_m)
+        return fail(h, SEEDCG_ERR_ARG, "requested rows are outside the stored basis");
+    if (count == 0) return SEEDCG_OK;
+    try {
+        const int vol = h->g.vol;
+        const long n = 12L * vol;
+        const size_t bytes = (size_t)count * n * sizeof(double2);
+        seedcg::DevBuf wide, canon;
+        wide.ensure(bytes);
+        double2* w = wide.as<double2>();
+        const size_t off = (size_t)first * n;
+        if (h->vbasis_prec == SEEDCG_FP64)
+            seedcg::convert<double2, double2>(h->vbasis.as<double2>() + off, w, count * n, 0);
+        else if (h->vbasis_prec == SEEDCG_MIXED_V32)
+            seedcg::convert<float2, double2>(h->vbasis.as<float2>() + off, w, count * n, 0);
+        else
+            seedcg::convert<__nv_bfloat162, double2>(h->vbasis.as<__nv_bfloat162>() + off, w, count * n, 0);
+        const bool od = is_device_ptr(out);
+        double* dst = out;
+        if (!od) {
+            canon.ensure(bytes);
+            dst = canon.as<double>();
+        }
+        seedcg::from_internal_f64(w, dst, vol, count, 0);
+        if (!od) SEEDCG_CUDA_TRY(cudaMemcpy(out, dst, bytes, cudaMemcpyDeviceToHost));
+        SEEDCG_CUDA_TRY(cudaDeviceSynchronize());
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+const char* seedcg_last_error(const seedcg_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void seedcg_destroy(seedcg_handle* h) {
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    h->u64.release();
+    h->u32.release();
+    h->vbasis.release();
+    h->lz_scalars.release();
+    h->red.release();
+    h->work.release();
+    h->coef.release();
+    h->staging.release();
+    if (h->pinned) cudaFreeHost(h->pinned);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+}  // extern "C"

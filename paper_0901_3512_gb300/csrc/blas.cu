@@ -1,0 +1,232 @@
+// BLAS-1 reductions and the SIMT projections against the stored basis:
+//   gemm_t:  C = A^dag B   (V^dag [v, f] for re-orthogonalisation, V^dag R_0 for seeds)
+//   gemm_n:  Y += A C      (the Gram-Schmidt subtraction, X = X_0 + V Y)
+// Vectors are flat arrays of complex entries in the internal order; inner
+// products do not depend on that order.
+#include "kernels.cuh"
+#include "reduce.cuh"
+
+namespace seedcg {
+
+namespace {
+
+inline int nblocks(long n, int per_block, int cap) {
+    long b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_dot(const cx_t<R>* __restrict__ a, const cx_t<R>* __restrict__ b, long n, double* partials,
+      unsigned* ctr, double2* res) {
+    double v[2] = {0.0, 0.0};
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> x = a[e], y = b[e];
+        v[0] += (double)x.x * y.x + (double)x.y * y.y;
+        v[1] += (double)x.x * y.y - (double)x.y * y.x;
+    }
+    grid_sum<2>(v, partials, ctr, [&](double* t) { *res = make_double2(t[0], t[1]); });
+}
+
+// ---------------------------------------------------------------------------
+// gemm_t: block (tile of TA rows of A) x (slice of the entries); every thread
+// keeps TA x NB complex accumulators in R, the block reduces them in FP64 and
+// writes one partial per (slice, row, column); k_gemm_t_fin sums the slices
+// in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename R, typename AT, int TA, int NB>
+__global__ void __launch_bounds__(kRedThreads)
+k_gemm_t(const AT* __restrict__ A, long lda, int na, const cx_t<R>* __restrict__ B, long ldb,
+         int nb, long n, double2* __restrict__ part) {
+    const int a0 = blockIdx.x * TA;
+    const int b0 = blockIdx.z * NB;
+    const long slice = (n + gridDim.y - 1) / gridDim.y;
+    const long e0 = blockIdx.y * slice;
+    const long e1 = e0 + slice < n ? e0 + slice : n;
+    cx_t<R> acc[TA][NB];
+#pragma unroll
+    for (int t = 0; t < TA; t++)
+#pragma unroll
+        for (int c = 0; c < NB; c++) acc[t][c] = mk<R>(0, 0);
+    for (long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        cx_t<R> bv[NB];
+#pragma unroll
+        for (int c = 0; c < NB; c++)
+            bv[c] = (b0 + c < nb) ? B[(size_t)(b0 + c) * ldb + e] : mk<R>(0, 0);
+#pragma unroll
+        for (int t = 0; t < TA; t++) {
+            if (a0 + t < na) {
+                cx_t<R> av = ld_cx<R>(A, (size_t)(a0 + t) * lda + e);
+#pragma unroll
+                for (int c = 0; c < NB; c++) acc[t][c] = cfma_conj(av, bv[c], acc[t][c]);
+            }
+        }
+    }
+    double v[2 * TA * NB];
+#pragma unroll
+    for (int t = 0; t < TA; t++)
+#pragma unroll
+        for (int c = 0; c < NB; c++) {
+            v[2 * (t * NB + c)] = acc[t][c].x;
+            v[2 * (t * NB + c) + 1] = acc[t][c].y;
+        }
+    block_sum<2 * TA * NB>(v);
+    // part layout [slice][a][b] with b over the full nb
+    for (int k = threadIdx.x; k < TA * NB; k += blockDim.x) {
+        int t = k / NB, c = k % NB;
+        if (a0 + t < na && b0 + c < nb)
+            part[((size_t)blockIdx.y * na + a0 + t) * nb + b0 + c] =
+                make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
+__global__ void k_gemm_t_fin(const double2* __restrict__ part, int nsplit, int na, int nb,
+                             double2* __restrict__ C, int ldc) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na * nb) return;
+    int a = k / nb, b = k % nb;
+    double2 s = make_double2(0.0, 0.0);
+    for (int p = 0; p < nsplit; p++) {
+        double2 z = part[((size_t)p * na + a) * nb + b];
+        s.x += z.x;
+        s.y += z.y;
+    }
+    C[(size_t)a * ldc + b] = s;
+}
+
+// ---------------------------------------------------------------------------
+// gemm_n: one thread per entry, loops over the rows of A (coalesced across the
+// warp for every row); the coefficients are staged in shared memory.
+// ---------------------------------------------------------------------------
+template <typename R, typename AT, typename YT, int NB>
+__global__ void __launch_bounds__(256)
+k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__ C, int ldc,
+         int nb, int b0, YT* __restrict__ Y, long ldy, long n, double sign) {
+    constexpr int CH = 128;
+    __shared__ cx_t<R> sc[CH][NB];
+    for (long base = blockIdx.x * (long)blockDim.x; base < n; base += (long)gridDim.x * blockDim.x) {
+        const long e = base + threadIdx.x;
+        cx_t<R> acc[NB];
+#pragma unroll
+        for (int c = 0; c < NB; c++) acc[c] = mk<R>(0, 0);
+        for (int a0 = 0; a0 < na; a0 += CH) {
+            int cnt = na - a0 < CH ? na - a0 : CH;
+            __syncthreads();
+            for (int k = threadIdx.x; k < CH * NB; k += blockDim.x) {
+                int a = k / NB, c = k % NB;
+                double2 z = (a < cnt && b0 + c < nb) ? C[(size_t)(a0 + a) * ldc + b0 + c]
+                                                     : make_double2(0.0, 0.0);
+                sc[a][c] = mk<R>((R)(sign * z.x), (R)(sign * z.y));
+            }
+            __syncthreads();
+            if (e < n) {
+                for (int a = 0; a < cnt; a++) {
+                    cx_t<R> av = ld_cx<R>(A, (size_t)(a0 + a) * lda + e);
+#pragma unroll
+                    for (int c = 0; c < NB; c++) acc[c] = cfma(av, sc[a][c], acc[c]);
+                }
+            }
+        }
+        if (e < n) {
+#pragma unroll
+            for (int c = 0; c < NB; c++) {
+                if (b0 + c < nb) {
+                    size_t idx = (size_t)(b0 + c) * ldy + e;
+                    cx_t<double> y = ld_cx<double>(Y, idx);
+                    st_cx(Y, idx, make_double2(y.x + (double)acc[c].x, y.y + (double)acc[c].y));
+                }
+            }
+        }
+    }
+}
+
+template <typename ST, typename DT>
+__global__ void k_convert(const ST* __restrict__ src, DT* __restrict__ dst, long n) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<double> z = ld_cx<double>(src, e);
+        st_cx(dst, e, z);
+    }
+}
+
+}  // namespace
+
+template <typename R>
+void dot(const cx_t<R>* a, const cx_t<R>* b, long n, double* partials, unsigned* ctr,
+         double2* res, cudaStream_t s) {
+    int nb = nblocks(n, kRedThreads * 8, kMaxRedBlocks);
+    k_dot<R><<<nb, kRedThreads, 0, s>>>(a, b, n, partials, ctr, res);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+template <typename R, typename AT>
+void gemm_t(const AT* A, long lda, int na, const cx_t<R>* B, long ldb, int nb, long n,
+            double2* C, int ldc, double2* scratch, size_t scratch_elems, cudaStream_t s) {
+    if (na <= 0 || nb <= 0) return;
+    constexpr int TA = sizeof(R) == 8 ? 4 : 8;
+    constexpr int NB = 2;
+    int tiles = (na + TA - 1) / TA;
+    int ctiles = (nb + NB - 1) / NB;
+    // enough blocks for ~4 waves on 152 SMs, each slice >= 4096 entries
+    long want = 2048 / ((long)tiles * ctiles) + 1;
+    long maxs = n / 4096 + 1;
+    long nsplit = want < maxs ? want : maxs;
+    long cap = (long)(scratch_elems / ((size_t)na * nb));
+    if (nsplit > cap) nsplit = cap;
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 65535) nsplit = 65535;
+    dim3 grid(tiles, (unsigned)nsplit, ctiles);
+    k_gemm_t<R, AT, TA, NB><<<grid, kRedThreads, 0, s>>>(A, lda, na, B, ldb, nb, n, scratch);
+    SEEDCG_CHECK_LAUNCH();
+    int tot = na * nb;
+    k_gemm_t_fin<<<(tot + 255) / 256, 256, 0, s>>>(scratch, (int)nsplit, na, nb, C, ldc);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+template <typename R, typename AT, typename YT>
+void gemm_n(const AT* A, long lda, int na, const double2* C, int ldc, int nb, YT* Y, long ldy,
+            long n, double sign, cudaStream_t s) {
+    if (na <= 0 || nb <= 0 || n <= 0) return;
+    int blocks = nblocks(n, 256, 152 * 16);
+    if (nb <= 2) {
+        k_gemm_n<R, AT, YT, 2><<<blocks, 256, 0, s>>>(A, lda, na, C, ldc, nb, 0, Y, ldy, n, sign);
+        SEEDCG_CHECK_LAUNCH();
+        return;
+    }
+    for (int b0 = 0; b0 < nb; b0 += 8) {
+        k_gemm_n<R, AT, YT, 8><<<blocks, 256, 0, s>>>(A, lda, na, C, ldc, nb, b0, Y, ldy, n, sign);
+        SEEDCG_CHECK_LAUNCH();
+    }
+}
+
+template <typename ST, typename DT>
+void convert(const ST* src, DT* dst, long n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_convert<ST, DT><<<nblocks(n, 256, 152 * 32), 256, 0, s>>>(src, dst, n);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+// explicit instantiations
+template void dot<double>(const double2*, const double2*, long, double*, unsigned*, double2*, cudaStream_t);
+template void dot<float>(const float2*, const float2*, long, double*, unsigned*, double2*, cudaStream_t);
+
+template void gemm_t<double, double2>(const double2*, long, int, const double2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+template void gemm_t<float, float2>(const float2*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+template void gemm_t<float, __nv_bfloat162>(const __nv_bfloat162*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+
+template void gemm_n<double, double2, double2>(const double2*, long, int, const double2*, int, int, double2*, long, long, double, cudaStream_t);
+template void gemm_n<float, float2, float2>(const float2*, long, int, const double2*, int, int, float2*, long, long, double, cudaStream_t);
+template void gemm_n<float, float2, double2>(const float2*, long, int, const double2*, int, int, double2*, long, long, double, cudaStream_t);
+template void gemm_n<float, __nv_bfloat162, float2>(const __nv_bfloat162*, long, int, const double2*, int, int, float2*, long, long, double, cudaStream_t);
+template void gemm_n<float, __nv_bfloat162, double2>(const __nv_bfloat162*, long, int, const double2*, int, int, double2*, long, long, double, cudaStream_t);
+
+template void convert<double2, double2>(const double2*, double2*, long, cudaStream_t);
+template void convert<float2, double2>(const float2*, double2*, long, cudaStream_t);
+template void convert<double2, float2>(const double2*, float2*, long, cudaStream_t);
+template void convert<__nv_bfloat162, double2>(const __nv_bfloat162*, double2*, long, cudaStream_t);
+template void convert<float2, float2>(const float2*, float2*, long, cudaStream_t);
+template void convert<float2, __nv_bfloat162>(const float2*, __nv_bfloat162*, long, cudaStream_t);
+
+}  // namespace seedcg

@@ -1,0 +1,1088 @@
+// Improved Seed-CG on the device (paper, Section 2, Algorithm 1):
+//   phase A  Lanczos for RHS 1 past convergence, with the LU of T (Eq. 2) kept
+//            on the device, periodic re-orthogonalisation every k iterations,
+//            and (literal mode) the per-iteration seed updates of steps 3-7;
+//   phase S  (blocked mode) the Galerkin seeds of Eq. (1) from the stored V;
+//   phase B  CG for every system whose FP64 true residual exceeds tol, all
+//            systems batched through the multi-RHS dslash, with FP64
+//            reliable updates in the mixed-precision modes.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "handle.cuh"
+#include "kernels.cuh"
+#include "reduce.cuh"
+#include "wilson.cuh"
+
+namespace seedcg {
+
+namespace {
+
+inline int red_blocks(long n) {
+    long b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+    if (b < 1) b = 1;
+    return (int)std::min<long>(b, 152 * 8);
+}
+
+inline int site_blocks(int vol) { return (vol + kRedThreads - 1) / kRedThreads; }
+
+// ===========================================================================
+// phase A kernels.  Every kernel of iteration i returns at once when i
+// exceeds the current target m (uniformly for the whole grid), so the host
+// may queue iterations ahead of its next poll.
+// ===========================================================================
+
+// Algorithm 1 step 9 bookkeeping after beta_i is final.
+__device__ void lz_after_beta(const LzDev& L, int i) {
+    LzCtl* c = L.ctl;
+    const double b = L.beta[i - 1], a = L.alpha[i - 1];
+    const double d = L.delta[i - 1], z = L.zeta[i - 1];
+    if (!isfinite(b) || !isfinite(d) || !isfinite(a)) {
+        c->status = SEEDCG_ERR_NAN;
+        c->m = i;
+        return;
+    }
+    const double est = b * fabs(z / d);
+    if (c->m_conv == 0 && est <= c->tol * c->bnorm1) {
+        c->m_conv = i;
+        int m1 = i + c->extra_iters;
+        int m2 = (int)ceil(c->past_factor * (double)i);
+        int m = m1 > m2 ? m1 : m2;
+        c->m = m < c->m_max ? m : c->m_max;
+    }
+    if (b <= 1e-14 * fabs(a)) {
+        c->breakdown = 1;
+        c->m = i;
+    }
+}
+
+// v_1 = r_0^1 / beta_0 (step 2); beta_0 already in ctl
+template <typename R>
+__global__ void k_lz_start(const cx_t<R>* __restrict__ r0, cx_t<R>* __restrict__ v, long n,
+                           LzDev L) {
+    const double inv = 1.0 / L.ctl->beta0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> z = r0[e];
+        v[e] = mk<R>((R)(z.x * inv), (R)(z.y * inv));
+    }
+}
+
+// t = D v_i
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_D(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restrict__ v,
+       cx_t<R>* __restrict__ t, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.vol) return;
+    const int vol = g.vol;
+    Nbr n = neighbours(g, s);
+    Spinor<R> acc, self, res;
+    auto load = [&](int y, Spinor<R>& p) { load_spinor(v, vol, y, p); };
+    auto fl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + s); };
+    auto bl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + n.b[mu]); };
+    hopping_sum<0, R>(n, load, fl, bl, acc);
+    load_spinor(v, vol, s, self);
+    wilson_combine(self, acc, kappa, res);
+    store_spinor(t, vol, s, res);
+}
+
+// Step 5 (and 2): f = D^dag t - beta_{i-1} v_{i-1}; alpha_i = Re v_i^dag f.
+// Step 6 scalars (and 3): gamma_{i-1}, delta_i, zeta_i.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_Ddag(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restrict__ t,
+          const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ vprev,
+          cx_t<R>* __restrict__ f, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    const int vol = g.vol;
+    const R bprev = i > 1 ? (R)L.beta[i - 2] : R(0);
+    double red[1] = {0.0};
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < vol) {
+        Nbr n = neighbours(g, s);
+        Spinor<R> acc, self, res;
+        auto load = [&](int y, Spinor<R>& p) { load_spinor(t, vol, y, p); };
+        auto fl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + s); };
+        auto bl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + n.b[mu]); };
+        hopping_sum<1, R>(n, load, fl, bl, acc);
+        load_spinor(t, vol, s, self);
+        wilson_combine(self, acc, kappa, res);
+        R part = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            cx_t<R> fv = res.c[k / 3][k % 3];
+            cx_t<R> vv = v[(size_t)k * vol + s];
+            if (i > 1) {
+                cx_t<R> pv = vprev[(size_t)k * vol + s];
+                fv.x -= bprev * pv.x;
+                fv.y -= bprev * pv.y;
+            }
+            f[(size_t)k * vol + s] = fv;
+            part += vv.x * fv.x + vv.y * fv.y;
+        }
+        red[0] = (double)part;
+    }
+    grid_sum<1>(red, L.partials, L.counters + CTR_B, [&](double* tot) {
+        const double a = tot[0];
+        L.alpha[i - 1] = a;
+        if (i == 1) {
+            L.delta[0] = a;
+            L.zeta[0] = L.ctl->beta0;
+        } else {
+            const double bp = L.beta[i - 2];
+            const double gm = bp / L.delta[i - 2];
+            L.gamma[i - 2] = gm;
+            L.delta[i - 1] = a - gm * bp;
+            L.zeta[i - 1] = -gm * L.zeta[i - 2];
+        }
+        if (L.delta[i - 1] == 0.0) {
+            L.ctl->status = SEEDCG_ERR_BREAKDOWN;
+            L.ctl->m = i;
+        }
+    });
+}
+
+// Steps 4 and 7 (literal seeding): eta^j = v_i^dag r_0^j - gamma_{i-1} eta^j for
+// j = j0 .. j0+NE-1 (r_0^j at r0 + (j-1) * n).
+template <typename R, int NE>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_eta(const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ r0, long n, int j0, int ne,
+         int i, LzDev L, unsigned* ctr) {
+    if (i > L.ctl->m) return;
+    double red[2 * NE];
+    R acc[2 * NE];
+#pragma unroll
+    for (int k = 0; k < 2 * NE; k++) acc[k] = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> a = v[e];
+#pragma unroll
+        for (int q = 0; q < NE; q++) {
+            if (q < ne) {
+                cx_t<R> b = r0[(size_t)(j0 + q - 1) * n + e];
+                acc[2 * q] += a.x * b.x + a.y * b.y;
+                acc[2 * q + 1] += a.x * b.y - a.y * b.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NE; k++) red[k] = (double)acc[k];
+    grid_sum<2 * NE>(red, L.partials, ctr, [&](double* tot) {
+        const double gm = i > 1 ? L.gamma[i - 2] : 0.0;
+        for (int q = 0; q < ne; q++) {
+            double2 old = L.eta[j0 + q - 2];
+            double2 nw;
+            nw.x = tot[2 * q] - (i > 1 ? gm * old.x : 0.0);
+            nw.y = tot[2 * q + 1] - (i > 1 ? gm * old.y : 0.0);
+            L.eta[j0 + q - 2] = nw;
+        }
+    });
+}
+
+// Steps 5-7 vector part: f -= alpha_i v_i; beta_i = ||f|| (final unless PO
+// follows).  Literal mode also: w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i,
+// x^1 += zeta_i w_i, x^j += eta^j w_i.
+template <typename R, bool LIT>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __restrict__ w,
+            cx_t<R>* __restrict__ X, int nrhs, long n, int i, int final_beta, LzDev L) {
+    if (i > L.ctl->m) return;
+    const R a = (R)L.alpha[i - 1];
+    R dl = 0, bp = 0, zt = 0;
+    if (LIT) {
+        dl = (R)L.delta[i - 1];
+        bp = i > 1 ? (R)L.beta[i - 2] : R(0);
+        zt = (R)L.zeta[i - 1];
+    }
+    R part = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> vv = v[e], fv = f[e];
+        fv.x -= a * vv.x;
+        fv.y -= a * vv.y;
+        f[e] = fv;
+        part += fv.x * fv.x + fv.y * fv.y;
+        if (LIT) {
+            cx_t<R> ww = i > 1 ? w[e] : mk<R>(0, 0);
+            ww.x = (vv.x - bp * ww.x) / dl;
+            ww.y = (vv.y - bp * ww.y) / dl;
+            w[e] = ww;
+            cx_t<R> x1 = X[e];
+            x1.x += zt * ww.x;
+            x1.y += zt * ww.y;
+            X[e] = x1;
+            for (int j = 1; j < nrhs; j++) {
+                double2 et = L.eta[j - 1];
+                cx_t<R> xj = X[(size_t)j * n + e];
+                xj = cfma(mk<R>((R)et.x, (R)et.y), ww, xj);
+                X[(size_t)j * n + e] = xj;
+            }
+        }
+    }
+    double red[1] = {(double)part};
+    grid_sum<1>(red, L.partials, L.counters + CTR_D, [&](double* tot) {
+        L.beta[i - 1] = sqrt(tot[0]);
+        if (final_beta) lz_after_beta(L, i);
+    });
+}
+
+// ---- step 8: periodic re-orthogonalisation (classical Gram-Schmidt) ----
+// [v, f] -= V_{1:i-1} c   with c = V^dag [v, f] already in coef (double2 [i-1][2]);
+// the columns of coef follow the order of the two rows passed to gemm_t.
+template <typename R, typename VT>
+__global__ void __launch_bounds__(kRedThreads)
+k_po_sub(const VT* __restrict__ V, long ldv, int na, const double2* __restrict__ coef, int cv,
+         cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    constexpr int CH = 128;
+    __shared__ cx_t<R> sc[CH][2];
+    R part = 0;
+    for (long base = blockIdx.x * (long)blockDim.x; base < n; base += (long)gridDim.x * blockDim.x) {
+        const long e = base + threadIdx.x;
+        cx_t<R> av = mk<R>(0, 0), af = mk<R>(0, 0);
+        for (int a0 = 0; a0 < na; a0 += CH) {
+            const int cnt = na - a0 < CH ? na - a0 : CH;
+            __syncthreads();
+            for (int k = threadIdx.x; k < 2 * CH; k += blockDim.x) {
+                int a = k >> 1, c = k & 1;
+                double2 z = a < cnt ? coef[(size_t)(a0 + a) * 2 + (c == 0 ? cv : 1 - cv)]
+                                    : make_double2(0.0, 0.0);
+                sc[a][c] = mk<R>((R)z.x, (R)z.y);
+            }
+            __syncthreads();
+            if (e < n) {
+                for (int a = 0; a < cnt; a++) {
+                    cx_t<R> x = ld_cx<R>(V, (size_t)(a0 + a) * ldv + e);
+                    av = cfma(x, sc[a][0], av);
+                    af = cfma(x, sc[a][1], af);
+                }
+            }
+        }
+        if (e < n) {
+            cx_t<R> vv = csub(v[e], av);
+            v[e] = vv;
+            f[e] = csub(f[e], af);
+            part += vv.x * vv.x + vv.y * vv.y;
+        }
+    }
+    double red[1] = {(double)part};
+    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) { L.ctl->nv = sqrt(tot[0]); });
+}
+
+// v_i /= ||v_i||; dvf = v_i^dag f
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_po_normalise(cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ f, long n, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    const R inv = (R)(1.0 / L.ctl->nv);
+    R pr = 0, pi = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> vv = cscale(v[e], inv);
+        v[e] = vv;
+        cx_t<R> fv = f[e];
+        pr += vv.x * fv.x + vv.y * fv.y;
+        pi += vv.x * fv.y - vv.y * fv.x;
+    }
+    double red[2] = {(double)pr, (double)pi};
+    grid_sum<2>(red, L.partials, L.counters + CTR_PO3,
+                [&](double* tot) { L.ctl->dvf = make_double2(tot[0], tot[1]); });
+}
+
+// f -= (v_i^dag f) v_i; beta_i = ||f||; step 9 bookkeeping
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_po_finish(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    const double2 d = L.ctl->dvf;
+    const cx_t<R> dc = mk<R>((R)d.x, (R)d.y);
+    R part = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> fv = csub(f[e], cmul(dc, v[e]));
+        f[e] = fv;
+        part += fv.x * fv.x + fv.y * fv.y;
+    }
+    double red[1] = {(double)part};
+    grid_sum<1>(red, L.partials, L.counters + CTR_PO4, [&](double* tot) {
+        L.beta[i - 1] = sqrt(tot[0]);
+        L.ctl->po_count += 1;
+        lz_after_beta(L, i);
+    });
+}
+
+// Step 9: store v_i into V (storage type VT); v_{i+1} = f / beta_i
+template <typename R, typename VT>
+__global__ void k_lz_advance(const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ f,
+                             cx_t<R>* __restrict__ vnext, VT* __restrict__ Vrow, long n, int i,
+                             LzDev L) {
+    if (i > L.ctl->m) return;
+    const double b = L.beta[i - 1];
+    const bool go = b > 0.0 && i < L.ctl->m;
+    const R inv = go ? (R)(1.0 / b) : R(0);
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> vv = v[e];
+        st_cx(Vrow, e, vv);
+        if (go) vnext[e] = cscale(f[e], inv);
+    }
+}
+
+// ||x||^2 of one flat vector into *out (FP64)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_norm2(const T* __restrict__ x, long n, double* partials, unsigned* ctr, double* out) {
+    double p = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<double> z = ld_cx<double>(x, e);
+        p += z.x * z.x + z.y * z.y;
+    }
+    double red[1] = {p};
+    grid_sum<1>(red, partials, ctr, [&](double* tot) { *out = sqrt(tot[0]); });
+}
+
+// ===========================================================================
+// phase S: Z = L^{-1} C, Y = U^{-1} Z column by column (Eq. 2 factors), in place
+// on C [m][ldc] double2.  One thread per right-hand side.
+// ===========================================================================
+__global__ void k_seed_tridiag(double2* C, int ldc, int nrhs, int m, LzDev L) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nrhs || m <= 0) return;
+    // forward: eta_1 = c_1, eta_i = c_i - gamma_{i-1} eta_{i-1}
+    double2 prev = C[j];
+    for (int i = 2; i <= m; i++) {
+        double gm = L.gamma[i - 2];
+        double2 c = C[(size_t)(i - 1) * ldc + j];
+        c.x -= gm * prev.x;
+        c.y -= gm * prev.y;
+        C[(size_t)(i - 1) * ldc + j] = c;
+        prev = c;
+    }
+    // back substitution with U (delta on, beta above the diagonal)
+    double2 y = C[(size_t)(m - 1) * ldc + j];
+    y.x /= L.delta[m - 1];
+    y.y /= L.delta[m - 1];
+    C[(size_t)(m - 1) * ldc + j] = y;
+    for (int i = m - 1; i >= 1; i--) {
+        double2 z = C[(size_t)(i - 1) * ldc + j];
+        double b = L.beta[i - 1];
+        z.x = (z.x - b * y.x) / L.delta[i - 1];
+        z.y = (z.y - b * y.y) / L.delta[i - 1];
+        C[(size_t)(i - 1) * ldc + j] = z;
+        y = z;
+    }
+}
+
+// ===========================================================================
+// phase B: batched CG.  Slot q works on system sys[q]; R-precision slot vectors
+// are [nslot][n]; FP64 solutions/right-hand sides are indexed by system.
+// ===========================================================================
+struct CgDev {
+    double* rr;       // [nslot] ||r||^2 of the iterated residual
+    double* rr_ru;    // [nslot] ||r||^2 at the last reliable update
+    double* alpha;    // [nslot]
+    double* beta;     // [nslot]
+    double* bn;       // [nslot] ||b||
+    int* active;      // [nslot]
+    int* flag;        // [nslot] 0 none, 1 reliable update due, 2 converged (check), 3 maxiter
+    int* iters;       // [nslot]
+    double* partials; // [nslot][blocks] * 2
+    unsigned* counters;  // [nslot]
+    double tol, delta2;
+    int maxiter;
+};
+
+// grid (blocks, nslot): each row reduces its own sums
+template <int NV, typename Fin>
+__device__ __forceinline__ void row_sum(double (&v)[NV], double* partials, unsigned* counters,
+                                        Fin fin) {
+    __shared__ bool s_last;
+    block_sum<NV>(v);
+    const unsigned nblk = gridDim.x, row = blockIdx.y;
+    double* part = partials + (size_t)row * NV * nblk;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) part[(size_t)k * nblk + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(counters + row, 1u);
+        s_last = (t == nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) tot[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; k++) tot[k] += __ldcg(part + (size_t)k * nblk + b);
+    block_sum<NV>(tot);
+    if (threadIdx.x == 0) {
+        fin(tot);
+        counters[row] = 0u;
+        __threadfence();
+    }
+}
+
+// alpha_q = rr_q / Re(p_q^dag q_q)
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_alpha(const cx_t<R>* __restrict__ P, const cx_t<R>* __restrict__ Q, long n, CgDev C) {
+    const int q = blockIdx.y;
+    if (!C.active[q]) return;
+    const cx_t<R>* p = P + (size_t)q * n;
+    const cx_t<R>* w = Q + (size_t)q * n;
+    R part = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> a = p[e], b = w[e];
+        part += a.x * b.x + a.y * b.y;
+    }
+    double red[1] = {(double)part};
+    row_sum<1>(red, C.partials, C.counters, [&](double* tot) { C.alpha[q] = C.rr[q] / tot[0]; });
+}
+
+// x += alpha p; r -= alpha q; rr_new = ||r||^2; beta = rr_new / rr; flags
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_xr(cx_t<R>* __restrict__ X, cx_t<R>* __restrict__ Rv, const cx_t<R>* __restrict__ P,
+        const cx_t<R>* __restrict__ Q, long n, CgDev C) {
+    const int q = blockIdx.y;
+    if (!C.active[q]) return;
+    const R a = (R)C.alpha[q];
+    cx_t<R>* x = X + (size_t)q * n;
+    cx_t<R>* r = Rv + (size_t)q * n;
+    const cx_t<R>* p = P + (size_t)q * n;
+    const cx_t<R>* w = Q + (size_t)q * n;
+    R part = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> pv = p[e], wv = w[e], xv = x[e], rv = r[e];
+        xv.x += a * pv.x; xv.y += a * pv.y;
+        rv.x -= a * wv.x; rv.y -= a * wv.y;
+        x[e] = xv;
+        r[e] = rv;
+        part += rv.x * rv.x + rv.y * rv.y;
+    }
+    double red[1] = {(double)part};
+    row_sum<1>(red, C.partials, C.counters, [&](double* tot) {
+        const double rn = tot[0];
+        C.beta[q] = rn / C.rr[q];
+        C.rr[q] = rn;
+        C.iters[q] += 1;
+        if (!isfinite(rn)) {
+            C.flag[q] = 3;
+            C.active[q] = 0;
+        } else if (sqrt(rn) <= C.tol * C.bn[q]) {
+            C.flag[q] = 2;
+            C.active[q] = 0;
+        } else if (C.iters[q] >= C.maxiter) {
+            C.flag[q] = 3;
+            C.active[q] = 0;
+        } else if (C.delta2 > 0.0 && rn < C.delta2 * C.rr_ru[q]) {
+            C.flag[q] = 1;
+        }
+    });
+}
+
+// p = r + beta p
+template <typename R>
+__global__ void k_cg_p(const cx_t<R>* __restrict__ Rv, cx_t<R>* __restrict__ P, long n, CgDev C) {
+    const int q = blockIdx.y;
+    if (!C.active[q]) return;
+    const R b = (R)C.beta[q];
+    const cx_t<R>* r = Rv + (size_t)q * n;
+    cx_t<R>* p = P + (size_t)q * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> rv = r[e], pv = p[e];
+        pv.x = rv.x + b * pv.x;
+        pv.y = rv.y + b * pv.y;
+        p[e] = pv;
+    }
+}
+
+// reliable update, part 1: x64[sys] += x_R[slot]; x_R[slot] = 0; gather x64[sys] -> G[k]
+template <typename R>
+__global__ void k_ru_flush(const int* __restrict__ slot, const int* __restrict__ sys,
+                           cx_t<R>* __restrict__ XR, double2* __restrict__ X64,
+                           double2* __restrict__ G, long n) {
+    const int k = blockIdx.y;
+    cx_t<R>* xr = XR + (size_t)slot[k] * n;
+    double2* x = X64 + (size_t)sys[k] * n;
+    double2* gk = G + (size_t)k * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> d = xr[e];
+        double2 xv = x[e];
+        xv.x += (double)d.x;
+        xv.y += (double)d.y;
+        x[e] = xv;
+        gk[e] = xv;
+        xr[e] = mk<R>(0, 0);
+    }
+}
+
+// reliable update, part 2: r64 = b - (M x)[k]; r_R[slot] = r64; rr = ||r64||^2
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_ru_resid(const int* __restrict__ slot, const int* __restrict__ sys,
+           const double2* __restrict__ B64, const double2* __restrict__ MX,
+           cx_t<R>* __restrict__ Rv, long n, CgDev C, double* __restrict__ tr_out,
+           double* partials, unsigned* counters) {
+    const int k = blockIdx.y;
+    const int q = slot[k], j = sys[k];
+    const double2* b = B64 + (size_t)j * n;
+    const double2* mx = MX + (size_t)k * n;
+    cx_t<R>* r = Rv + (size_t)q * n;
+    double part = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        double2 bv = b[e], mv = mx[e];
+        double rx = bv.x - mv.x, ry = bv.y - mv.y;
+        r[e] = mk<R>((R)rx, (R)ry);
+        part += rx * rx + ry * ry;
+    }
+    double red[1] = {part};
+    row_sum<1>(red, partials, counters, [&](double* tot) {
+        const double rn = tot[0];
+        C.rr[q] = rn;
+        C.rr_ru[q] = rn;
+        C.flag[q] = 0;
+        tr_out[j] = C.bn[q] > 0.0 ? sqrt(rn) / C.bn[q] : 0.0;
+        C.active[q] = (C.bn[q] > 0.0 && sqrt(rn) > C.tol * C.bn[q]) ? 1 : 0;
+    });
+}
+
+// M x for n FP64 fields in internal layout (D then D^dag) via the multi-RHS kernel
+inline void apply_M64(seedcg_handle* h, int n, const double2* x, double2* tmp, double2* out,
+                      cudaStream_t st) {
+    dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, n, x, tmp, st);
+    dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, n, tmp, out, st);
+}
+
+template <typename R>
+inline void apply_M_mrhs(seedcg_handle* h, int n, const cx_t<R>* x, cx_t<R>* tmp, cx_t<R>* out,
+                         cudaStream_t st);
+template <>
+inline void apply_M_mrhs<double>(seedcg_handle* h, int n, const double2* x, double2* tmp,
+                                 double2* out, cudaStream_t st) {
+    apply_M64(h, n, x, tmp, out, st);
+}
+template <>
+inline void apply_M_mrhs<float>(seedcg_handle* h, int n, const float2* x, float2* tmp,
+                                float2* out, cudaStream_t st) {
+    dslash_mrhs_f32(h->g, h->u32.as<float2>(), (float)h->kappa, 0, n, x, tmp, st);
+    dslash_mrhs_f32(h->g, h->u32.as<float2>(), (float)h->kappa, 1, n, tmp, out, st);
+}
+
+// bump allocator over one device buffer
+struct Carve {
+    char* base;
+    size_t off = 0, cap;
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        if (off > cap) throw Error{SEEDCG_ERR_OOM, "workspace carve overflow"};
+        return p;
+    }
+};
+
+struct PhaseTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = 0.f;
+    void start(cudaStream_t s) {
+        if (!a) { cudaEventCreate(&a); cudaEventCreate(&b); }
+        cudaEventRecord(a, s);
+    }
+    void stop(cudaStream_t s) { cudaEventRecord(b, s); }
+    float read() {
+        if (!a) return 0.f;
+        cudaEventSynchronize(b);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        return t;
+    }
+    ~PhaseTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+
+// r0 = b - mx (mx may be null), narrowed to R
+template <typename R>
+__global__ void k_resid_init(const double2* __restrict__ b, const double2* __restrict__ mx,
+                             cx_t<R>* __restrict__ r0, long n) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        double2 z = b[e];
+        if (mx) {
+            double2 w = mx[e];
+            z.x -= w.x;
+            z.y -= w.y;
+        }
+        r0[e] = mk<R>((R)z.x, (R)z.y);
+    }
+}
+
+// ===========================================================================
+// host driver, templated on working precision R and basis storage VT
+// ===========================================================================
+struct CgHost {
+    std::vector<int> sys;         // slot -> system
+    std::vector<int> iters;       // per system
+    std::vector<int> ru;          // reliable updates per system
+    std::vector<int> notconv;     // per system
+};
+
+template <typename R, typename VT>
+seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2* X64,
+                        double tol, int extra_iters, int k_po, seedcg_info* info,
+                        cudaStream_t st) {
+    const seedcg_options& o = h->opt;
+    const int vol = h->g.vol;
+    const long n = 12L * vol;
+    const bool fp64 = sizeof(R) == 8;
+    const bool literal = (o.seed_mode == 0) && fp64;
+    const int m_max = std::max(o.m_max, 1);
+    const int poll = o.poll_every > 0 ? o.poll_every : 32;
+    const R kap = (R)h->kappa;
+    const cx_t<R>* U = fp64 ? reinterpret_cast<const cx_t<R>*>(h->u64.p)
+                            : reinterpret_cast<const cx_t<R>*>(h->u32.p);
+
+    // ---------------- workspaces ----------------
+    const size_t cxR = sizeof(cx_t<R>);
+    size_t need = 0;
+    auto add = [&](size_t bytes) { need += ((bytes + 255) & ~(size_t)255); };
+    for (int k = 0; k < 5; k++) add(n * cxR);                   // vA f vB t w
+    for (int k = 0; k < 6; k++) add((size_t)nrhs * n * cxR);    // R0 XR Rr P Q T
+    for (int k = 0; k < 3; k++) add((size_t)nrhs * n * sizeof(double2));  // G MX T64
+    h->work.ensure(need + 8192);
+    Carve cv{h->work.as<char>(), 0, h->work.bytes};
+    cx_t<R>* vA = cv.take<cx_t<R>>(n);
+    cx_t<R>* fv = cv.take<cx_t<R>>(n);
+    cx_t<R>* vB = cv.take<cx_t<R>>(n);
+    cx_t<R>* tv = cv.take<cx_t<R>>(n);
+    cx_t<R>* wv = cv.take<cx_t<R>>(n);
+    cx_t<R>* R0 = cv.take<cx_t<R>>((size_t)nrhs * n);
+    cx_t<R>* XR = cv.take<cx_t<R>>((size_t)nrhs * n);
+    cx_t<R>* Rr = cv.take<cx_t<R>>((size_t)nrhs * n);
+    cx_t<R>* Pv = cv.take<cx_t<R>>((size_t)nrhs * n);
+    cx_t<R>* Qv = cv.take<cx_t<R>>((size_t)nrhs * n);
+    cx_t<R>* Tv = cv.take<cx_t<R>>((size_t)nrhs * n);
+    double2* G = cv.take<double2>((size_t)nrhs * n);
+    double2* MX = cv.take<double2>((size_t)nrhs * n);
+    double2* T64 = cv.take<double2>((size_t)nrhs * n);
+    if (fv != vA + n || vB != fv + n)
+        throw Error{SEEDCG_ERR_ARG, "internal: working vectors are not contiguous"};
+
+    // Lanczos scalars
+    const size_t ms = (size_t)m_max + 2;
+    h->lz_scalars.ensure(sizeof(LzCtl) + 5 * sizeof(double) * ms + sizeof(double2) * (nrhs + 2) +
+                         sizeof(double) * 8 * (nrhs + 2) + sizeof(int) * 8 * (nrhs + 2) + 8192);
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(h->lz_scalars.p, 0, h->lz_scalars.bytes, st));
+    Carve cs{h->lz_scalars.as<char>(), 0, h->lz_scalars.bytes};
+    LzDev L;
+    L.ctl = cs.take<LzCtl>(1);
+    L.alpha = cs.take<double>(ms);
+    L.beta = cs.take<double>(ms);
+    L.delta = cs.take<double>(ms);
+    L.gamma = cs.take<double>(ms);
+    L.zeta = cs.take<double>(ms);
+    L.eta = cs.take<double2>(nrhs + 2);
+    double* bnorm = cs.take<double>(nrhs + 2);
+    double* tr_dev = cs.take<double>(nrhs + 2);
+    // CG scalars
+    CgDev C;
+    C.rr = cs.take<double>(nrhs + 2);
+    C.rr_ru = cs.take<double>(nrhs + 2);
+    C.alpha = cs.take<double>(nrhs + 2);
+    C.beta = cs.take<double>(nrhs + 2);
+    C.bn = cs.take<double>(nrhs + 2);
+    C.active = cs.take<int>(nrhs + 2);
+    C.flag = cs.take<int>(nrhs + 2);
+    C.iters = cs.take<int>(nrhs + 2);
+    int* ru_slot = cs.take<int>(nrhs + 2);
+    int* ru_sys = cs.take<int>(nrhs + 2);
+
+    const int rb = red_blocks(n);
+    const size_t part_doubles = (size_t)std::max(kMaxRedBlocks, rb * (nrhs + 2)) * 64;
+    h->red.ensure(part_doubles * sizeof(double) + 8192 * sizeof(unsigned));
+    L.partials = h->red.as<double>();
+    L.counters = reinterpret_cast<unsigned*>(h->red.as<double>() + part_doubles);
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(L.counters, 0, 8192 * sizeof(unsigned), st));
+    C.partials = L.partials;
+    C.counters = L.counters + 1024;
+    C.tol = tol;
+    C.delta2 = fp64 ? 0.0 : o.reliable_delta * o.reliable_delta;
+    C.maxiter = o.cg_maxiter;
+
+    // V basis and coefficient scratch
+    const size_t vrow = (size_t)n * sizeof(VT);
+    h->vbasis.ensure(vrow * (size_t)m_max);
+    VT* Vb = h->vbasis.as<VT>();
+    h->vbasis_prec = o.precision;
+    h->vbasis_m = 0;
+    const size_t cols = (size_t)std::max(nrhs, 2);
+    const size_t coef_elems = ms * cols;
+    const size_t split_elems = std::max<size_t>(coef_elems * 48, (size_t)1 << 20);
+    h->coef.ensure((coef_elems + split_elems) * sizeof(double2));
+    double2* Cc = h->coef.as<double2>();
+    double2* split = Cc + coef_elems;
+
+    // pinned host scratch: [0,256) slot lists / flags, [256,512) system lists,
+    // [512,1024) active flags, [1024] a zero, doubles from int 2048 on
+    int* pin = reinterpret_cast<int*>(h->pinned);
+    double* pind = reinterpret_cast<double*>(pin + 2048);
+    pin[1024] = 0;
+
+    PhaseTimer t_all, t_lz, t_seed, t_cg;
+    t_all.start(st);
+
+    // ---------------- step 1: r_0^j = b^j - M x_0^j ----------------
+    const int nbl = std::min<long>((n * nrhs + 255) / 256, 152 * 32);
+    if (o.x0_given) {
+        apply_M64(h, nrhs, X64, T64, MX, st);
+        k_resid_init<R><<<nbl, 256, 0, st>>>(B64, MX, R0, n * nrhs);
+    } else {
+        k_resid_init<R><<<nbl, 256, 0, st>>>(B64, nullptr, R0, n * nrhs);
+    }
+    SEEDCG_CHECK_LAUNCH();
+    for (int j = 0; j < nrhs; j++) {
+        k_norm2<double2><<<rb, kRedThreads, 0, st>>>(B64 + (size_t)j * n, n, L.partials,
+                                                     L.counters + CTR_NORM, bnorm + j);
+        SEEDCG_CHECK_LAUNCH();
+    }
+    k_norm2<cx_t<R>><<<rb, kRedThreads, 0, st>>>(R0, n, L.partials, L.counters + CTR_NORM,
+                                                  &L.ctl->beta0);
+    SEEDCG_CHECK_LAUNCH();
+    {
+        LzCtl hc;
+        memset(&hc, 0, sizeof(hc));
+        hc.m = m_max;
+        hc.m_max = m_max;
+        hc.extra_iters = extra_iters;
+        hc.tol = tol;
+        hc.past_factor = o.past_factor;
+        // copy everything but beta0 / bnorm1 (set on the device)
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(L.ctl, &hc, offsetof(LzCtl, beta0), cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(&L.ctl->tol, &hc.tol, sizeof(double) * 2, cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(&L.ctl->bnorm1, bnorm, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(pind, &L.ctl->beta0, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const double beta0 = pind[0];
+
+    // ---------------- phase A: Lanczos for RHS 1 ----------------
+    t_lz.start(st);
+    float ms_po = 0.f;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> po_ev;
+    int m = 0, m_conv = 0, po_count = 0, lz_status = SEEDCG_OK, breakdown = 0;
+    if (beta0 > 0.0) {
+        const int sb = site_blocks(vol);
+        k_lz_start<R><<<rb, kRedThreads, 0, st>>>(R0, vA, n, L);
+        SEEDCG_CHECK_LAUNCH();
+        cx_t<R>* v = vA;
+        cx_t<R>* vprev = vB;
+        int i = 1;
+        for (; i <= m_max; i++) {
+            k_lz_D<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, v, tv, i, L);
+            SEEDCG_CHECK_LAUNCH();
+            k_lz_Ddag<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, tv, v, vprev, fv, i, L);
+            SEEDCG_CHECK_LAUNCH();
+            if (literal) {
+                for (int j0 = 2; j0 <= nrhs; j0 += 8) {
+                    int ne = std::min(8, nrhs - j0 + 1);
+                    k_lz_eta<R, 8><<<rb, kRedThreads, 0, st>>>(v, R0, n, j0, ne, i, L,
+                                                                 L.counters + CTR_ETA0 + j0);
+                    SEEDCG_CHECK_LAUNCH();
+                }
+            }
+            const bool po_now = k_po > 0 && i >= 2 && (i % k_po) == 0;
+            if (literal)
+                k_lz_update<R, true><<<rb, kRedThreads, 0, st>>>(v, fv, wv, reinterpret_cast<cx_t<R>*>(X64),
+                                                               nrhs, n, i, po_now ? 0 : 1, L);
+            else
+                k_lz_update<R, false><<<rb, kRedThreads, 0, st>>>(v, fv, wv, nullptr, nrhs, n, i,
+                                                                po_now ? 0 : 1, L);
+            SEEDCG_CHECK_LAUNCH();
+            if (po_now) {
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+                const int na = i - 1;
+                const cx_t<R>* Bst = (v == vA) ? vA : fv;  // rows [v, f] or [f, v]
+                const int cvcol = (v == vA) ? 0 : 1;
+                for (int pass = 0; pass < std::max(o.po_passes, 1); pass++) {
+                    gemm_t<R, VT>(Vb, n, na, Bst, n, 2, n, Cc, 2, split, split_elems, st);
+                    k_po_sub<R, VT><<<rb, kRedThreads, 0, st>>>(Vb, n, na, Cc, cvcol, v, fv, n, i, L);
+                    SEEDCG_CHECK_LAUNCH();
+                }
+                k_po_normalise<R><<<rb, kRedThreads, 0, st>>>(v, fv, n, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                k_po_finish<R><<<rb, kRedThreads, 0, st>>>(v, fv, n, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                cudaEventRecord(e1, st);
+                po_ev.push_back({e0, e1});
+            }
+            k_lz_advance<R, VT><<<rb, kRedThreads, 0, st>>>(v, fv, vprev, Vb + (size_t)(i - 1) * n, n,
+                                                           i, L);
+            SEEDCG_CHECK_LAUNCH();
+            std::swap(v, vprev);
+            if (i % poll == 0 || i == m_max) {
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, L.ctl, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+                SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+                if (i >= pin[0]) break;
+            }
+        }
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, L.ctl, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        m = std::min(pin[0], m_max);
+        m_conv = pin[1];
+        lz_status = pin[2];
+        breakdown = pin[3];
+        po_count = pin[4];
+        for (auto& pe : po_ev) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pe.first, pe.second);
+            ms_po += t;
+            cudaEventDestroy(pe.first);
+            cudaEventDestroy(pe.second);
+        }
+        // keep the scalars of T for seedcg_get_lanczos
+        h->alpha.assign(m, 0.0);
+        h->beta.assign(m, 0.0);
+        h->delta.assign(m, 0.0);
+        if (m > 0) {
+            SEEDCG_CUDA_TRY(cudaMemcpy(h->alpha.data(), L.alpha, sizeof(double) * m, cudaMemcpyDeviceToHost));
+            SEEDCG_CUDA_TRY(cudaMemcpy(h->beta.data(), L.beta, sizeof(double) * m, cudaMemcpyDeviceToHost));
+            SEEDCG_CUDA_TRY(cudaMemcpy(h->delta.data(), L.delta, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        }
+    }
+    h->last_m = m;
+    h->vbasis_m = m;
+    t_lz.stop(st);
+    (void)breakdown;
+
+    // ---------------- phase S: Galerkin seeds, Eq. (1) ----------------
+    t_seed.start(st);
+    if (!literal && m > 0) {
+        gemm_t<R, VT>(Vb, n, m, R0, n, nrhs, n, Cc, nrhs, split, split_elems, st);
+        k_seed_tridiag<<<(nrhs + 63) / 64, 64, 0, st>>>(Cc, nrhs, nrhs, m, L);
+        SEEDCG_CHECK_LAUNCH();
+        gemm_n<R, VT, double2>(Vb, n, m, Cc, nrhs, nrhs, X64, n, n, 1.0, st);
+    }
+    t_seed.stop(st);
+
+    // ---------------- phase B: batched CG ----------------
+    t_cg.start(st);
+    CgHost ch;
+    ch.iters.assign(nrhs, 0);
+    ch.ru.assign(nrhs, 0);
+    ch.notconv.assign(nrhs, 0);
+    int reliable_updates = 0;
+    if (!o.stop_after_seed) {
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(XR, 0, (size_t)nrhs * n * cxR, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.bn, bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
+        // reliable update over a list of (slot, system) pairs
+        auto reliable = [&](const std::vector<int>& slots) {
+            const int nf = (int)slots.size();
+            for (int k = 0; k < nf; k++) {
+                pin[k] = slots[k];
+                pin[256 + k] = ch.sys[slots[k]];
+            }
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_slot, pin, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_sys, pin + 256, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+            dim3 gr(rb, nf);
+            k_ru_flush<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, XR, X64, G, n);
+            SEEDCG_CHECK_LAUNCH();
+            apply_M64(h, nf, G, T64, MX, st);
+            k_ru_resid<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, B64, MX, Rr, n, C, tr_dev,
+                                                      C.partials, C.counters);
+            SEEDCG_CHECK_LAUNCH();
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin + 512 + 0, C.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int k = 0; k < nf; k++) {
+                ch.ru[ch.sys[slots[k]]] += 1;
+                reliable_updates++;
+            }
+        };
+        int nslot = nrhs;
+        ch.sys.resize(nrhs);
+        for (int j = 0; j < nrhs; j++) ch.sys[j] = j;
+        std::vector<int> all(nrhs);
+        for (int j = 0; j < nrhs; j++) all[j] = j;
+        if (nrhs > 256) throw Error{SEEDCG_ERR_ARG, "nrhs > 256 is not supported"};
+        reliable(all);
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv, Rr, (size_t)nrhs * n * cxR, cudaMemcpyDeviceToDevice, st));
+        std::vector<int> act(pin + 512, pin + 512 + nrhs);
+
+        auto compact = [&]() {
+            // download per-slot scalars, keep the active slots in front
+            std::vector<double> hd(5 * nslot);
+            std::vector<int> hi(3 * nslot);
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 0 * nslot, C.rr, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 1 * nslot, C.rr_ru, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 2 * nslot, C.bn, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hi.data() + 0 * nslot, C.iters, sizeof(int) * nslot, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int> keep;
+            for (int q = 0; q < nslot; q++) {
+                ch.iters[ch.sys[q]] += hi[q];
+                if (act[q]) keep.push_back(q);
+            }
+            const int nk = (int)keep.size();
+            std::vector<double> nrr(nk), nru(nk), nbn(nk);
+            std::vector<int> nsys(nk), zeros(nk, 0), ones(nk, 1);
+            for (int k = 0; k < nk; k++) {
+                int q = keep[k];
+                nrr[k] = hd[q];
+                nru[k] = hd[nslot + q];
+                nbn[k] = hd[2 * nslot + q];
+                nsys[k] = ch.sys[q];
+                if (q != k) {
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(XR + (size_t)k * n, XR + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(Rr + (size_t)k * n, Rr + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv + (size_t)k * n, Pv + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                }
+            }
+            if (nk > 0) {
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr, nrr.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr_ru, nru.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.bn, nbn.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.iters, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.flag, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active, ones.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+            }
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            ch.sys = nsys;
+            nslot = nk;
+            act.assign(nk, 1);
+        };
+        compact();
+        // iteration counts continue per system across compactions; maxiter is
+        // enforced per stretch between compactions against the running total
+        while (nslot > 0) {
+            {
+                // per-slot remaining iteration budget
+                int minleft = o.cg_maxiter;
+                for (int q = 0; q < nslot; q++) minleft = std::min(minleft, o.cg_maxiter - ch.iters[ch.sys[q]]);
+                C.maxiter = std::max(minleft, 1);
+            }
+            for (int it = 0; it < poll; it++) {
+                apply_M_mrhs<R>(h, nslot, Pv, Tv, Qv, st);
+                dim3 gr(rb, nslot);
+                k_cg_alpha<R><<<gr, kRedThreads, 0, st>>>(Pv, Qv, n, C);
+                SEEDCG_CHECK_LAUNCH();
+                k_cg_xr<R><<<gr, kRedThreads, 0, st>>>(XR, Rr, Pv, Qv, n, C);
+                SEEDCG_CHECK_LAUNCH();
+                k_cg_p<R><<<gr, kRedThreads, 0, st>>>(Rr, Pv, n, C);
+                SEEDCG_CHECK_LAUNCH();
+            }
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, C.flag, sizeof(int) * nslot, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int> flags(pin, pin + nslot);
+            std::vector<int> fl;
+            for (int q = 0; q < nslot; q++)
+                if (flags[q]) fl.push_back(q);
+            if (!fl.empty()) {
+                reliable(fl);
+                std::vector<int> a2(pin + 512, pin + 512 + nslot);
+                for (int q : fl) {
+                    if (flags[q] == 3) {
+                        // iteration cap or non-finite residual: stop this system
+                        ch.notconv[ch.sys[q]] = 1;
+                        a2[q] = 0;
+                        SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active + q, pin + 1024, sizeof(int), cudaMemcpyHostToDevice, st));
+                    } else if (flags[q] == 2 && a2[q]) {
+                        // the iterated residual converged but the true one did not: restart
+                        SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv + (size_t)q * n, Rr + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                    }
+                }
+                act = a2;
+                bool any_done = false;
+                for (int q = 0; q < nslot; q++) any_done |= !act[q];
+                if (any_done) compact();
+            }
+        }
+    }
+    t_cg.stop(st);
+    t_all.stop(st);
+
+    // ---------------- results ----------------
+    std::vector<double> tr(nrhs, 0.0);
+    if (!o.stop_after_seed)
+        SEEDCG_CUDA_TRY(cudaMemcpy(tr.data(), tr_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+    seedcg_status code = SEEDCG_OK;
+    if (lz_status == SEEDCG_ERR_NAN) code = SEEDCG_ERR_NAN;
+    else if (lz_status == SEEDCG_ERR_BREAKDOWN) code = SEEDCG_ERR_BREAKDOWN;
+    if (!o.stop_after_seed && code == SEEDCG_OK) {
+        for (int j = 0; j < nrhs; j++)
+            if (ch.notconv[j] || !(tr[j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
+    }
+    if (info) {
+        info->m_conv = m_conv;
+        info->m = m;
+        info->po_count = po_count;
+        int mx = 0;
+        for (int j = 0; j < nrhs; j++) mx = std::max(mx, ch.iters[j]);
+        info->cg_iters_max = mx;
+        info->reliable_updates = reliable_updates;
+        for (int j = 0; j < nrhs; j++) {
+            if (info->iters) info->iters[j] = ch.iters[j] + (j == 0 ? m : 0);
+            if (info->matvecs)
+                info->matvecs[j] = 2 * (ch.iters[j] + ch.ru[j]) + (j == 0 ? 2 * m : 0) + (o.x0_given ? 2 : 0);
+            if (info->true_resid) info->true_resid[j] = tr[j];
+        }
+        info->ms_total = t_all.read();
+        info->ms_lanczos = t_lz.read();
+        info->ms_po = ms_po;
+        info->ms_seed = t_seed.read();
+        info->ms_cg = t_cg.read();
+    }
+    return code;
+}
+
+}  // namespace
+
+seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
+                         int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {
+    // B, X: device canonical complex128 (the API layer stages host pointers)
+    const int vol = h->g.vol;
+    const long n = 12L * vol;
+    const size_t fb = (size_t)nrhs * n * sizeof(double2);
+    h->staging.ensure(2 * fb + 512);
+    double2* B64 = h->staging.as<double2>();
+    double2* X64 = B64 + (size_t)nrhs * n;
+    to_internal_f64(B, B64, vol, nrhs, st);
+    if (h->opt.x0_given)
+        to_internal_f64(X, X64, vol, nrhs, st);
+    else
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(X64, 0, fb, st));
+    seedcg_status code;
+    switch (h->opt.precision) {
+        case SEEDCG_FP64:
+            code = run_solve<double, double2>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
+            break;
+        case SEEDCG_MIXED_V32:
+            code = run_solve<float, float2>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
+            break;
+        default:
+            code = run_solve<float, __nv_bfloat162>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
+            break;
+    }
+    from_internal_f64(X64, X, vol, nrhs, st);
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return code;
+}
+
+}  // namespace seedcg

@@ -1,0 +1,177 @@
+// Device-side Wilson hopping term, shared by the dslash kernels and the fused
+// solver kernels.
+//
+//   (D psi)(x) = psi(x) - kappa sum_mu [ P-_mu U_mu(x) psi(x+mu) s_f
+//                                      + P+_mu U_mu(x-mu)^dag psi(x-mu) s_b ]
+//   P-_mu = 1 - g_mu,  P+_mu = 1 + g_mu,  s = -1 on hops that wrap t.
+//   D^dag = g5 D g5 swaps P- and P+ (g5 anticommutes with every g_mu).
+//
+// Each projector has rank 2 in spin space, so a hop projects the 4-spinor to
+// two colour vectors h0, h1, multiplies them by the link and rebuilds the
+// other two spin components from them.  In the chiral basis
+// g_k = [[0,-i s_k],[i s_k,0]], g_4 = [[0,1],[1,0]] the projections for
+// P = 1 + S g_mu (S = +-1) are
+//   mu=x: h0 = p0 - S i p3, h1 = p1 - S i p2;  full = (r0, r1,  S i r1,  S i r0)
+//   mu=y: h0 = p0 - S   p3, h1 = p1 + S   p2;  full = (r0, r1,  S   r1, -S   r0)
+//   mu=z: h0 = p0 - S i p2, h1 = p1 + S i p3;  full = (r0, r1,  S i r0, -S i r1)
+//   mu=t: h0 = p0 + S   p2, h1 = p1 + S   p3;  full = (r0, r1,  S   r0,  S   r1)
+#pragma once
+
+#include "internal.cuh"
+
+namespace seedcg {
+
+template <typename R> struct Spinor { cx_t<R> c[4][3]; };
+
+// h = (1 + S g_mu) p, two colour vectors
+template <int MU, int S, typename R>
+__device__ __forceinline__ void spin_project(const Spinor<R>& p, cx_t<R> h[2][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (MU == 0) {
+            h[0][a] = S > 0 ? csub(p.c[0][a], ci(p.c[3][a])) : cadd(p.c[0][a], ci(p.c[3][a]));
+            h[1][a] = S > 0 ? csub(p.c[1][a], ci(p.c[2][a])) : cadd(p.c[1][a], ci(p.c[2][a]));
+        } else if (MU == 1) {
+            h[0][a] = S > 0 ? csub(p.c[0][a], p.c[3][a]) : cadd(p.c[0][a], p.c[3][a]);
+            h[1][a] = S > 0 ? cadd(p.c[1][a], p.c[2][a]) : csub(p.c[1][a], p.c[2][a]);
+        } else if (MU == 2) {
+            h[0][a] = S > 0 ? csub(p.c[0][a], ci(p.c[2][a])) : cadd(p.c[0][a], ci(p.c[2][a]));
+            h[1][a] = S > 0 ? cadd(p.c[1][a], ci(p.c[3][a])) : csub(p.c[1][a], ci(p.c[3][a]));
+        } else {
+            h[0][a] = S > 0 ? cadd(p.c[0][a], p.c[2][a]) : csub(p.c[0][a], p.c[2][a]);
+            h[1][a] = S > 0 ? cadd(p.c[1][a], p.c[3][a]) : csub(p.c[1][a], p.c[3][a]);
+        }
+    }
+}
+
+// acc += coef * (full spinor rebuilt from r) for P = 1 + S g_mu
+template <int MU, int S, typename R>
+__device__ __forceinline__ void spin_accum(Spinor<R>& acc, const cx_t<R> r[2][3], R coef) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cx_t<R> r0 = cscale(r[0][a], coef), r1 = cscale(r[1][a], coef);
+        acc.c[0][a] = cadd(acc.c[0][a], r0);
+        acc.c[1][a] = cadd(acc.c[1][a], r1);
+        if (MU == 0) {
+            acc.c[2][a] = S > 0 ? cadd(acc.c[2][a], ci(r1)) : csub(acc.c[2][a], ci(r1));
+            acc.c[3][a] = S > 0 ? cadd(acc.c[3][a], ci(r0)) : csub(acc.c[3][a], ci(r0));
+        } else if (MU == 1) {
+            acc.c[2][a] = S > 0 ? cadd(acc.c[2][a], r1) : csub(acc.c[2][a], r1);
+            acc.c[3][a] = S > 0 ? csub(acc.c[3][a], r0) : cadd(acc.c[3][a], r0);
+        } else if (MU == 2) {
+            acc.c[2][a] = S > 0 ? cadd(acc.c[2][a], ci(r0)) : csub(acc.c[2][a], ci(r0));
+            acc.c[3][a] = S > 0 ? csub(acc.c[3][a], ci(r1)) : cadd(acc.c[3][a], ci(r1));
+        } else {
+            acc.c[2][a] = S > 0 ? cadd(acc.c[2][a], r0) : csub(acc.c[2][a], r0);
+            acc.c[3][a] = S > 0 ? cadd(acc.c[3][a], r1) : csub(acc.c[3][a], r1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spinor loads/stores in the internal layouts
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void load_spinor(const cx_t<R>* __restrict__ p, int vol, int s,
+                                            Spinor<R>& out) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) out.c[k / 3][k % 3] = __ldg(p + (size_t)k * vol + s);
+}
+template <typename R>
+__device__ __forceinline__ void store_spinor(cx_t<R>* __restrict__ p, int vol, int s,
+                                             const Spinor<R>& v) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) p[(size_t)k * vol + s] = v.c[k / 3][k % 3];
+}
+
+// ---------------------------------------------------------------------------
+// neighbours
+// ---------------------------------------------------------------------------
+struct Nbr {
+    int f[4], b[4];
+    bool fwrap_t, bwrap_t;
+};
+
+__device__ __forceinline__ Nbr neighbours(const Geom& g, int s) {
+    Nbr n;
+    int c[4];
+    int r = s;
+    c[0] = r % g.L[0]; r /= g.L[0];
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2]; r /= g.L[2];
+    c[3] = r;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        n.f[mu] = (c[mu] == g.L[mu] - 1) ? s - (g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
+        n.b[mu] = (c[mu] == 0) ? s + (g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
+    }
+    n.fwrap_t = (c[3] == g.L[3] - 1);
+    n.bwrap_t = (c[3] == 0);
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// one hop: acc += coef * P U psi_nbr  (forward: U = U_mu(x); backward: U = U_mu(x-mu)^dag)
+// LinkAt(a, b) returns U[a][b] for the link in use.
+// ---------------------------------------------------------------------------
+template <int MU, int S, bool BACK, typename R, typename LinkAt>
+__device__ __forceinline__ void hop(Spinor<R>& acc, const Spinor<R>& nb, LinkAt link, R coef) {
+    cx_t<R> h[2][3], r[2][3];
+    spin_project<MU, S>(nb, h);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cx_t<R> r0 = mk<R>(0, 0), r1 = mk<R>(0, 0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (!BACK) {
+                cx_t<R> u = link(a, b);
+                r0 = cfma(u, h[0][b], r0);
+                r1 = cfma(u, h[1][b], r1);
+            } else {
+                cx_t<R> u = link(b, a);
+                r0 = cfma_conj(u, h[0][b], r0);
+                r1 = cfma_conj(u, h[1][b], r1);
+            }
+        }
+        r[0][a] = r0;
+        r[1][a] = r1;
+    }
+    spin_accum<MU, S>(acc, r, coef);
+}
+
+// Hopping sum H psi at site s (without the -kappa and the identity term).
+// Fwd(mu, e) / Bwd(mu, e) give element e = 3a+b of U_mu(x) / U_mu(x-mu).
+template <int DAG, typename R, typename LoadNbr, typename Fwd, typename Bwd>
+__device__ __forceinline__ void hopping_sum(const Nbr& n, LoadNbr load, Fwd fl, Bwd bl,
+                                            Spinor<R>& acc) {
+    constexpr int SF = DAG ? 1 : -1;   // forward projector 1 - g (D) or 1 + g (D^dag)
+    constexpr int SB = -SF;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) acc.c[a][b] = mk<R>(0, 0);
+    Spinor<R> nb;
+    load(n.f[0], nb); hop<0, SF, false>(acc, nb, [&](int a, int b) { return fl(0, 3 * a + b); }, R(1));
+    load(n.b[0], nb); hop<0, SB, true>(acc, nb, [&](int a, int b) { return bl(0, 3 * a + b); }, R(1));
+    load(n.f[1], nb); hop<1, SF, false>(acc, nb, [&](int a, int b) { return fl(1, 3 * a + b); }, R(1));
+    load(n.b[1], nb); hop<1, SB, true>(acc, nb, [&](int a, int b) { return bl(1, 3 * a + b); }, R(1));
+    load(n.f[2], nb); hop<2, SF, false>(acc, nb, [&](int a, int b) { return fl(2, 3 * a + b); }, R(1));
+    load(n.b[2], nb); hop<2, SB, true>(acc, nb, [&](int a, int b) { return bl(2, 3 * a + b); }, R(1));
+    load(n.f[3], nb); hop<3, SF, false>(acc, nb, [&](int a, int b) { return fl(3, 3 * a + b); }, n.fwrap_t ? R(-1) : R(1));
+    load(n.b[3], nb); hop<3, SB, true>(acc, nb, [&](int a, int b) { return bl(3, 3 * a + b); }, n.bwrap_t ? R(-1) : R(1));
+}
+
+// out = in - kappa * H
+template <typename R>
+__device__ __forceinline__ void wilson_combine(const Spinor<R>& in, const Spinor<R>& hsum, R kappa,
+                                               Spinor<R>& out) {
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            out.c[a][b].x = fma(-kappa, hsum.c[a][b].x, in.c[a][b].x);
+            out.c[a][b].y = fma(-kappa, hsum.c[a][b].y, in.c[a][b].y);
+        }
+}
+
+}  // namespace seedcg

@@ -1,0 +1,248 @@
+"""Thin Python binding of libseedcg (include/seedcg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device memory for inputs and outputs comes from PyTorch tensors
+(complex128, on the GPU); host numpy arrays are also accepted where the C
+ABI accepts host pointers.  There is no CPU fallback: if the library or a
+GPU is missing, loading or the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+SEEDCG_OK = 0
+SEEDCG_ERR_ARG = -1
+SEEDCG_ERR_OOM = -2
+SEEDCG_ERR_CUDA = -3
+SEEDCG_ERR_NOT_CONVERGED = -4
+SEEDCG_ERR_BREAKDOWN = -5
+SEEDCG_ERR_NAN = -6
+SEEDCG_ERR_TIMEOUT = -7
+
+SEEDCG_FP64 = 0
+SEEDCG_MIXED_V32 = 1
+SEEDCG_MIXED_VBF16 = 2
+PRECISIONS = {"fp64": SEEDCG_FP64, "mixed_v32": SEEDCG_MIXED_V32, "mixed_vbf16": SEEDCG_MIXED_VBF16}
+
+OP_D, OP_DDAG, OP_M = 0, 1, 2
+
+
+class seedcg_options(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int), ("past_factor", ctypes.c_double),
+                ("precision", ctypes.c_int), ("reliable_delta", ctypes.c_double),
+                ("po_passes", ctypes.c_int), ("seed_mode", ctypes.c_int),
+                ("x0_given", ctypes.c_int), ("cg_maxiter", ctypes.c_int),
+                ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int)]
+
+
+class seedcg_info(ctypes.Structure):
+    _fields_ = [("m_conv", ctypes.c_int), ("m", ctypes.c_int), ("po_count", ctypes.c_int),
+                ("cg_iters_max", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("iters", ctypes.POINTER(ctypes.c_int)),
+                ("matvecs", ctypes.POINTER(ctypes.c_int)),
+                ("true_resid", ctypes.POINTER(ctypes.c_double)),
+                ("ms_total", ctypes.c_float), ("ms_lanczos", ctypes.c_float),
+                ("ms_po", ctypes.c_float), ("ms_seed", ctypes.c_float), ("ms_cg", ctypes.c_float)]
+
+
+_lib = None
+
+# every entry point of include/seedcg.h, for the export check
+EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "seedcg_solve",
+           "seedcg_apply", "seedcg_get_lanczos", "seedcg_get_basis", "seedcg_last_error",
+           "seedcg_destroy"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libseedcg.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise RuntimeError(f"libseedcg not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    hpp = ctypes.POINTER(ctypes.c_void_p)
+    lib.seedcg_default_options.argtypes = [ctypes.POINTER(seedcg_options)]
+    lib.seedcg_default_options.restype = None
+    lib.seedcg_create.argtypes = [hpp, ip, vp, ctypes.c_double, ctypes.POINTER(seedcg_options)]
+    lib.seedcg_set_options.argtypes = [vp, ctypes.POINTER(seedcg_options)]
+    lib.seedcg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_int, ctypes.POINTER(seedcg_info), vp]
+    lib.seedcg_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 vp, vp, vp]
+    lib.seedcg_get_lanczos.argtypes = [vp, ctypes.c_int, dp, dp, dp, ip]
+    lib.seedcg_get_basis.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.seedcg_last_error.argtypes = [vp]
+    lib.seedcg_last_error.restype = ctypes.c_char_p
+    lib.seedcg_destroy.argtypes = [vp]
+    lib.seedcg_destroy.restype = None
+    for name in ("seedcg_create", "seedcg_set_options", "seedcg_solve", "seedcg_apply",
+                 "seedcg_get_lanczos", "seedcg_get_basis"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class SeedCGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"seedcg status {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a) -> int:
+    """Data pointer of a torch tensor (device or host) or a numpy array."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def seedcg_default_options() -> seedcg_options:
+    o = seedcg_options()
+    load().seedcg_default_options(ctypes.byref(o))
+    return o
+
+
+def seedcg_last_error(h) -> str:
+    m = load().seedcg_last_error(h)
+    return m.decode() if m else ""
+
+
+def _check(h, code: int, allow=()):
+    if code != SEEDCG_OK and code not in allow:
+        raise SeedCGError(code, seedcg_last_error(h))
+    return code
+
+
+def seedcg_create(dims: Sequence[int], gauge, kappa: float, opt: Optional[seedcg_options] = None):
+    lib = load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    code = lib.seedcg_create(ctypes.byref(h), d, ctypes.c_void_p(_ptr(gauge)), float(kappa),
+                             ctypes.byref(opt) if opt is not None else None)
+    if code != SEEDCG_OK:
+        raise SeedCGError(code, seedcg_last_error(None))
+    return h
+
+
+def seedcg_set_options(h, opt: seedcg_options):
+    _check(h, load().seedcg_set_options(h, ctypes.byref(opt)))
+
+
+def seedcg_solve(h, nrhs: int, B, X, tol: float, extra_iters: int, reorth_period: int,
+                 stream=None, allow_not_converged: bool = False):
+    """Returns (status, info dict).  B, X: complex128 [nrhs][V][4][3], host or device."""
+    info = seedcg_info()
+    iters = (ctypes.c_int * nrhs)()
+    mv = (ctypes.c_int * nrhs)()
+    tr = (ctypes.c_double * nrhs)()
+    info.iters = iters
+    info.matvecs = mv
+    info.true_resid = tr
+    code = load().seedcg_solve(h, int(nrhs), ctypes.c_void_p(_ptr(B)), ctypes.c_void_p(_ptr(X)),
+                               float(tol), int(extra_iters), int(reorth_period),
+                               ctypes.byref(info), _stream_ptr(stream))
+    _check(h, code, allow=(SEEDCG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    out = {"status": code, "m_conv": info.m_conv, "m": info.m, "po_count": info.po_count,
+           "cg_iters_max": info.cg_iters_max, "reliable_updates": info.reliable_updates,
+           "iters": list(iters), "matvecs": list(mv), "true_resid": list(tr),
+           "ms_total": info.ms_total, "ms_lanczos": info.ms_lanczos, "ms_po": info.ms_po,
+           "ms_seed": info.ms_seed, "ms_cg": info.ms_cg}
+    return code, out
+
+
+def seedcg_apply(h, op: int, prec: int, multi: int, n: int, inp, out, stream=None):
+    _check(h, load().seedcg_apply(h, int(op), int(prec), int(multi), int(n),
+                                  ctypes.c_void_p(_ptr(inp)), ctypes.c_void_p(_ptr(out)),
+                                  _stream_ptr(stream)))
+
+
+def seedcg_get_lanczos(h, cap: int):
+    a = np.zeros(cap)
+    b = np.zeros(cap)
+    d = np.zeros(cap)
+    m = ctypes.c_int()
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(h, load().seedcg_get_lanczos(h, int(cap), a.ctypes.data_as(dp), b.ctypes.data_as(dp),
+                                        d.ctypes.data_as(dp), ctypes.byref(m)))
+    k = min(cap, m.value)
+    return a[:k], b[:k], d[:k], m.value
+
+
+def seedcg_get_basis(h, first: int, count: int, out):
+    _check(h, load().seedcg_get_basis(h, int(first), int(count), ctypes.c_void_p(_ptr(out))))
+
+
+def seedcg_destroy(h):
+    if h:
+        load().seedcg_destroy(h)
+
+
+def make_options(**kw) -> seedcg_options:
+    """Defaults of the C library, with fields overridden by keyword."""
+    o = seedcg_default_options()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """Convenience owner of one handle (one gauge field)."""
+
+    def __init__(self, dims, gauge, kappa, **opts):
+        self.dims = tuple(int(d) for d in dims)
+        self.vol = int(np.prod(self.dims))
+        self.h = seedcg_create(self.dims, gauge, kappa, make_options(**opts) if opts else None)
+
+    def set_options(self, **opts):
+        seedcg_set_options(self.h, make_options(**opts))
+
+    def solve(self, B, X, tol=1e-8, extra_iters=0, reorth_period=10, stream=None,
+              allow_not_converged=False):
+        nrhs = B.shape[0]
+        return seedcg_solve(self.h, nrhs, B, X, tol, extra_iters, reorth_period, stream,
+                            allow_not_converged)
+
+    def apply(self, op, inp, out, prec=0, multi=0, stream=None):
+        n = inp.shape[0] if len(inp.shape) == 4 else 1
+        seedcg_apply(self.h, op, prec, multi, n, inp, out, stream)
+
+    def close(self):
+        if self.h:
+            seedcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

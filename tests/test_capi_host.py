@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point that
+include/seedcg.h declares, and rejects bad arguments before touching a GPU
+(CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_0901_3512_gb300 import build, seedcg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "seedcg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(seedcg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = seedcg.load()
+    declared = _declared()
+    assert len(declared) >= 9
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in seedcg.h but not exported"
+    assert sorted(seedcg.EXPORTS) == sorted(n for n in declared if n in seedcg.EXPORTS)
+    assert set(declared) <= set(seedcg.EXPORTS), "binding misses an entry point"
+
+
+def test_default_options_are_host_only():
+    o = seedcg.seedcg_default_options()
+    assert o.m_max == 4000 and o.past_factor == 1.0 and o.precision == seedcg.SEEDCG_FP64
+    assert o.reliable_delta == pytest.approx(0.1) and o.po_passes == 1 and o.seed_mode == 1
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 4, 4), (4, 4, 4, 0), (4, 4, 4, 1)])
+def test_create_rejects_bad_dims_before_device_work(dims):
+    g = np.zeros(max(1, int(np.prod(dims))) * 36, dtype=np.complex128)
+    with pytest.raises(seedcg.SeedCGError) as e:
+        seedcg.seedcg_create(dims, g, 0.1)
+    assert e.value.code == seedcg.SEEDCG_ERR_ARG
+
+
+def test_create_rejects_bad_options():
+    g = np.zeros(16 * 36, dtype=np.complex128)
+    for kw in ({"past_factor": 0.5}, {"precision": 7}, {"po_passes": 3},
+               {"seed_mode": 0, "precision": "mixed_v32"}, {"m_max": 0}):
+        with pytest.raises(seedcg.SeedCGError) as e:
+            seedcg.seedcg_create((2, 2, 2, 2), g, 0.1, seedcg.make_options(**kw))
+        assert e.value.code == seedcg.SEEDCG_ERR_ARG
+
+
+def test_solve_and_apply_reject_null_handle():
+    lib = seedcg.load()
+    assert lib.seedcg_solve(None, 1, None, None, 1e-8, 0, 10, None, None) == seedcg.SEEDCG_ERR_ARG
+    assert lib.seedcg_apply(None, 0, 0, 0, 1, None, None, None) == seedcg.SEEDCG_ERR_ARG
+    assert b"NULL" in lib.seedcg_last_error(None)
+    lib.seedcg_destroy(None)  # no-op

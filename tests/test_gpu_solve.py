@@ -1,0 +1,193 @@
+"""Parity of the CUDA Improved Seed-CG with the oracle (Section 2, Algorithm 1
+and Eq. 1-2), through the C-ABI.
+
+Bars (from the method's specification): FP64 GPU vs FP64 oracle solutions
+within 1e-6 relative at tol = 1e-8, every true residual <= tol recomputed in
+FP64, iteration counts within 2%.  The Lanczos scalars of T and the seeded
+guesses are compared before CG as well.  Mixed-precision modes must meet the
+same residual bar; their distance to the oracle is bounded by cond(M) * tol
+(several correct solutions exist within that distance)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.seedcg import improved_seed_cg, seed_lanczos, galerkin_seed
+from oracle.wilson import WilsonOperator
+from paper_0901_3512_gb300 import seedcg, workloads as W
+from tests.gpu_helpers import dev, host, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def _tiny():
+    wl = W.WORKLOADS["tiny_4x4x4x4_nrhs4"]
+    f = wl.fields[0]
+    u = f.gauge()
+    kappa = W.kappa_for(f.name)
+    op = WilsonOperator(f.dims, u, kappa)
+    eta = wl.sources_for(0)
+    B = np.stack([op.Ddag(e) for e in eta]).reshape(len(eta), -1)
+    return f.dims, u, kappa, op, eta, B, wl
+
+
+def _gpu_B(s, eta):
+    out = dev(np.zeros_like(eta))
+    s.apply(seedcg.OP_DDAG, dev(eta), out, prec=0, multi=1)
+    return out
+
+
+def _within(a, b, frac=0.02):
+    return abs(a - b) <= max(1, math.ceil(frac * max(a, b)))
+
+
+@pytest.mark.parametrize("seed_mode", [0, 1])
+def test_tiny_fp64_lanczos_scalars_and_seeds(seed_mode):
+    need_gpu()
+    dims, u, kappa, op, eta, B, wl = _tiny()
+    ref = seed_lanczos(op.M, B, None, TOL, 4000, wl.reorth_period, wl.past_factor)
+    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, seed_mode=seed_mode,
+                      stop_after_seed=1, precision="fp64")
+    Bd = _gpu_B(s, eta)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(Bd, X, TOL, 0, wl.reorth_period)
+    assert info["m_conv"] == ref.m_conv and info["m"] == ref.m
+    assert info["po_count"] == ref.po_count
+    a, b, d, m = seedcg.seedcg_get_lanczos(s.h, 10000)
+    k = min(40, m)
+    assert np.allclose(a[:k], ref.alpha[:k], rtol=1e-10, atol=0)
+    assert np.allclose(b[:k], ref.beta[:k], rtol=1e-10, atol=0)
+    assert np.allclose(d[:k], ref.delta[:k], rtol=1e-10, atol=0)
+    want = ref.X if seed_mode == 0 else galerkin_seed(ref.V, ref.alpha, ref.beta, ref.R0)
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        assert rel(got[j], want[j]) <= 1e-8, (j, rel(got[j], want[j]))
+    # the stored basis is the oracle's, and orthonormal after the last PO step
+    Vg = dev(np.zeros((m,) + eta.shape[1:], dtype=np.complex128))
+    seedcg.seedcg_get_basis(s.h, 0, m, Vg)
+    Vg = host(Vg).reshape(m, -1)
+    assert rel(Vg[:20], ref.V[:20]) <= 1e-10
+    last = (m // wl.reorth_period) * wl.reorth_period
+    G = Vg[:last].conj() @ Vg[:last].T
+    assert np.abs(G - np.eye(last)).max() <= 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("seed_mode", [0, 1])
+def test_tiny_fp64_full_solve_matches_oracle(seed_mode):
+    need_gpu()
+    dims, u, kappa, op, eta, B, wl = _tiny()
+    ref = improved_seed_cg(op.M, B, None, TOL, 4000, wl.reorth_period, wl.past_factor,
+                           seed_mode="literal" if seed_mode == 0 else "blocked")
+    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, seed_mode=seed_mode)
+    Bd = _gpu_B(s, eta)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(Bd, X, TOL, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        assert info["true_resid"][j] <= TOL
+        tr = np.linalg.norm(B[j] - op.M(got[j])) / np.linalg.norm(B[j])
+        assert tr <= TOL, (j, tr)
+        assert rel(got[j], ref.X[j]) <= 1e-6
+        assert _within(info["iters"][j], int(ref.iters[j])), (j, info["iters"], ref.iters)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed_v32", "mixed_vbf16"])
+def test_tiny_mixed_meets_residual_bar(precision):
+    need_gpu()
+    dims, u, kappa, op, eta, B, wl = _tiny()
+    Md = op.dense(WilsonOperator.OP_M)
+    ev = np.linalg.eigvalsh(Md)
+    cond = ev[-1] / ev[0]
+    Xd = np.linalg.solve(Md, B.T).T
+    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, precision=precision)
+    Bd = _gpu_B(s, eta)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(Bd, X, TOL, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        tr = np.linalg.norm(B[j] - Md @ got[j]) / np.linalg.norm(B[j])
+        assert tr <= TOL
+        assert rel(got[j], Xd[j]) <= cond * TOL
+    assert info["reliable_updates"] >= len(eta)
+    s.close()
+
+
+def test_edge_cases_ragged_lattice():
+    """Ragged 6x4x4x6 lattice; nrhs = 1; a zero first right-hand side; a given x0."""
+    need_gpu()
+    dims = (6, 4, 4, 6)
+    u = W.gauge_field(dims, 0.5, 8)
+    kappa = 0.19
+    op = WilsonOperator(dims, u, kappa)
+    eta = W.z2_sources(dims, 3, 8)
+    B = np.stack([op.Ddag(e) for e in eta])
+    s = seedcg.Solver(dims, u, kappa, past_factor=1.2)
+    # nrhs = 1
+    X = dev(np.zeros_like(B[:1]))
+    code, info = s.solve(dev(B[:1]), X, TOL, 0, 10)
+    assert code == 0 and info["true_resid"][0] <= TOL
+    ref = improved_seed_cg(op.M, B[:1].reshape(1, -1), None, TOL, 4000, 10, 1.2)
+    assert info["m"] == ref.seed.m and rel(host(X), ref.X) <= 1e-6
+    # zero first right-hand side: no Lanczos, the others solved by CG from zero
+    Bz = B.copy()
+    Bz[0] = 0
+    X = dev(np.zeros_like(Bz))
+    code, info = s.solve(dev(Bz), X, TOL, 0, 10)
+    assert code == 0 and info["m"] == 0
+    got = host(X)
+    assert np.all(got[0] == 0)
+    for j in (1, 2):
+        assert np.linalg.norm(B[j] - op.M(got[j])) <= TOL * np.linalg.norm(B[j])
+    # x0 given (a perturbed solution): r0 = b - M x0
+    Xs = np.stack([np.linalg.solve(op.dense(WilsonOperator.OP_M), b.reshape(-1)) for b in B])
+    X0 = (Xs * (1 + 1e-3)).reshape(B.shape)
+    s.set_options(past_factor=1.2, x0_given=1)
+    X = dev(X0)
+    code, info = s.solve(dev(B), X, TOL, 0, 10)
+    assert code == 0
+    got = host(X)
+    for j in range(3):
+        assert np.linalg.norm(B[j] - op.M(got[j])) <= TOL * np.linalg.norm(B[j])
+    # host (numpy) buffers work through the same entry point
+    s.set_options(past_factor=1.2)
+    Xh = np.zeros_like(B)
+    code, info = s.solve(np.ascontiguousarray(B), Xh, TOL, 0, 10)
+    assert code == 0 and info["true_resid"][2] <= TOL
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_v32"])
+def test_small_8x8x8x16_point_sources(precision):
+    """The 8^3x16, 12-point-source workload at full size against the oracle."""
+    need_gpu()
+    wl = W.WORKLOADS["small_8x8x8x16_nrhs12"]
+    f = wl.fields[0]
+    u = f.gauge()
+    kappa = W.kappa_for(f.name)
+    op = WilsonOperator(f.dims, u, kappa)
+    eta = wl.sources_for(0)
+    B = np.stack([op.Ddag(e) for e in eta]).reshape(len(eta), -1)
+    ref = improved_seed_cg(op.M, B, None, TOL, 6000, wl.reorth_period, wl.past_factor,
+                           seed_mode="blocked")
+    s = seedcg.Solver(f.dims, u, kappa, past_factor=wl.past_factor, precision=precision,
+                      m_max=6000)
+    Bd = _gpu_B(s, eta)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(Bd, X, TOL, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        assert info["true_resid"][j] <= TOL
+        assert np.linalg.norm(B[j] - op.M(got[j])) <= TOL * np.linalg.norm(B[j])
+    if precision == "fp64":
+        assert _within(info["m_conv"], ref.seed.m_conv)
+        for j in range(len(eta)):
+            assert rel(got[j], ref.X[j]) <= 1e-6
+            assert _within(info["iters"][j], int(ref.iters[j])), (j, info["iters"], ref.iters)
+    s.close()
