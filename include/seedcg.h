@@ -76,6 +76,7 @@ typedef struct {
     int cg_maxiter;        /* CG iteration cap per system (default 20000)               */
     int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */
     int poll_every;        /* iterations between host polls of device flags (default 32) */
+    int use_tensor_cores;  /* 1: bf16-basis projections V^dag X on tcgen05 (default), 0: SIMT */
 } seedcg_options;
 
 typedef struct {
@@ -149,6 +150,30 @@ seedcg_status seedcg_get_lanczos(const seedcg_handle* h, int cap, double* alpha,
  * V precision (the stored values are widened).
  */
 seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* out);
+
+/*
+ * After a solve: C[a][j] = v_a^dag x_j, the projection of nvec spinor fields
+ * onto the first `rows` stored basis vectors (the contraction that Algorithm 1
+ * step 8 and Eq. (1) perform against V).  X: device, complex128 [nvec][V][4][3];
+ * C: host, complex128 [rows][nvec].  use_tensor_cores = 1 takes the tcgen05
+ * path when V is stored in bf16 (x_j rounded to bf16 for the product), 0 the
+ * SIMT path (x_j rounded to the working precision).
+ */
+seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const double* X,
+                                   double* C, int use_tensor_cores, void* stream);
+
+/*
+ * Measurement helper: time `reps` launches of the multi-RHS dslash D on n
+ * internal spinor fields (prec 0 = FP64, 1 = FP32) with CUDA events on
+ * `stream`, writing a 512 MB buffer between launches when flush_l2 != 0 so
+ * that every launch starts from a cold L2.  *ms_per_launch receives the mean.
+ */
+seedcg_status seedcg_time_dslash(seedcg_handle* h, int prec, int n, int reps, int flush_l2,
+                                 float* ms_per_launch, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+   handles, all threads); differences around a call count its launches. */
+unsigned long long seedcg_kernel_launches(void);
 
 /* Message for the last failing call on h (never NULL). */
 const char* seedcg_last_error(const seedcg_handle* h);

@@ -77,7 +77,6 @@ def tune(dims, gauge, target, log=print):
 def main(argv):
     names = argv or list(W.FIELDS)
     path = W._KAPPA_FILE
-    table = W.kappa_table()
     for name in names:
         f = W.FIELDS[name]
         print(f"tuning {name} dims={f.dims} eps={f.eps} seed={f.seed} target={f.cond_target:g}",
@@ -85,13 +84,14 @@ def main(argv):
         g = f.gauge()
         t0 = time.time()
         k, c = tune(f.dims, g, f.cond_target, log=lambda s: print(s, flush=True))
+        table = W.kappa_table()  # merge with entries other runs wrote meanwhile
         table[name] = {"kappa": k, "cond": c[0], "lam_min": c[1], "lam_max": c[2],
                        "lanczos_iters": c[3], "target": f.cond_target,
                        "method": "dense eigvalsh" if c[3] == 0 else "Lanczos extreme Ritz values",
                        "seconds": round(time.time() - t0, 1)}
-        with open(path + ".tmp", "w") as fh:
+        with open(path + f".tmp{os.getpid()}", "w") as fh:
             json.dump(table, fh, indent=1, sort_keys=True)
-        os.replace(path + ".tmp", path)
+        os.replace(path + f".tmp{os.getpid()}", path)
         print(f"  -> kappa={k:.6f} cond={c[0]:.4g}", flush=True)
 
 

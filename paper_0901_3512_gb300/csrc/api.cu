@@ -10,6 +10,10 @@
 
 using seedcg::Error;
 
+namespace seedcg {
+std::atomic<unsigned long long> g_kernel_launches{0};
+}
+
 namespace {
 
 constexpr size_t kPinnedBytes = 64 * 1024;
@@ -41,6 +45,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.seed_mode == 0 && o.precision != SEEDCG_FP64) { why = "literal seeding (seed_mode 0) needs precision FP64"; return false; }
     if (o.cg_maxiter < 1) { why = "cg_maxiter must be >= 1"; return false; }
     if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
+    if (o.use_tensor_cores < 0 || o.use_tensor_cores > 1) { why = "use_tensor_cores must be 0 or 1"; return false; }
     return true;
 }
 
@@ -61,6 +66,7 @@ void seedcg_default_options(seedcg_options* opt) {
     opt->cg_maxiter = 20000;
     opt->stop_after_seed = 0;
     opt->poll_every = 32;
+    opt->use_tensor_cores = 1;
 }
 
 seedcg_status seedcg_create(seedcg_handle** out, const int dims[4], const double* gauge,
@@ -156,6 +162,7 @@ seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* 
             const char* what = code == SEEDCG_ERR_NOT_CONVERGED ? "a system did not converge"
                              : code == SEEDCG_ERR_BREAKDOWN ? "delta_i = 0 in the LU of T (M not HPD?)"
                              : code == SEEDCG_ERR_NAN ? "NaN/Inf in a Lanczos scalar"
+                             : code == SEEDCG_ERR_TIMEOUT ? "a bounded device wait expired"
                              : "solve failed";
             h->err = what;
         }
@@ -271,6 +278,71 @@ seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* o
     }
 }
 
+seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const double* X,
+                                   double* C, int use_tensor_cores, void* stream) {
+    if (!h || !X || !C) return fail(h, SEEDCG_ERR_ARG, "h, X or C is NULL");
+    if (rows < 1 || rows > h->vbasis_m || nvec < 1 || nvec > 32)
+        return fail(h, SEEDCG_ERR_ARG, "rows must be in [1, stored basis size], nvec in [1, 32]");
+    if (!is_device_ptr(X)) return fail(h, SEEDCG_ERR_ARG, "X must be a device pointer");
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        seedcg_status c = seedcg::project_basis_impl(h, rows, nvec, X, C, use_tensor_cores ? 1 : 0,
+                                                     reinterpret_cast<cudaStream_t>(stream));
+        if (c != SEEDCG_OK) h->err = "a bounded device wait expired";
+        return c;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_time_dslash(seedcg_handle* h, int prec, int n, int reps, int flush_l2,
+                                float* ms_per_launch, void* stream) {
+    if (!h || !ms_per_launch) return fail(h, SEEDCG_ERR_ARG, "h or ms_per_launch is NULL");
+    if (prec < 0 || prec > 1 || n < 1 || reps < 1) return fail(h, SEEDCG_ERR_ARG, "bad prec/n/reps");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        const int vol = h->g.vol;
+        const size_t nf = (size_t)n * vol * 12;
+        const size_t esz = prec == 0 ? sizeof(double2) : sizeof(float2);
+        seedcg::DevBuf buf, flush;
+        buf.ensure(2 * nf * esz + 512);
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(buf.p, 0, 2 * nf * esz, st));
+        const size_t fbytes = (size_t)512 << 20;  // 4x the 129 MB L2
+        if (flush_l2) flush.ensure(fbytes);
+        char* b0 = buf.as<char>();
+        cudaEvent_t e0, e1;
+        SEEDCG_CUDA_TRY(cudaEventCreate(&e0));
+        SEEDCG_CUDA_TRY(cudaEventCreate(&e1));
+        float tot = 0.f;
+        for (int r = 0; r < reps + 1; r++) {
+            if (flush_l2) SEEDCG_CUDA_TRY(cudaMemsetAsync(flush.p, r & 0xff, fbytes, st));
+            SEEDCG_CUDA_TRY(cudaEventRecord(e0, st));
+            if (prec == 0)
+                seedcg::dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, n,
+                                        (const double2*)b0, (double2*)(b0 + nf * esz), st);
+            else
+                seedcg::dslash_mrhs_f32(h->g, h->u32.as<float2>(), (float)h->kappa, 0, n,
+                                        (const float2*)b0, (float2*)(b0 + nf * esz), st);
+            SEEDCG_CUDA_TRY(cudaEventRecord(e1, st));
+            SEEDCG_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            SEEDCG_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (r > 0) tot += t;  // the first launch is a warm-up
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *ms_per_launch = tot / reps;
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+unsigned long long seedcg_kernel_launches(void) {
+    return seedcg::g_kernel_launches.load(std::memory_order_relaxed);
+}
+
 const char* seedcg_last_error(const seedcg_handle* h) {
     if (!h) return g_create_error.c_str();
     return h->err.c_str();
@@ -288,6 +360,7 @@ void seedcg_destroy(seedcg_handle* h) {
     h->red.release();
     h->work.release();
     h->coef.release();
+    h->tcbuf.release();
     h->staging.release();
     if (h->pinned) cudaFreeHost(h->pinned);
     cudaSetDevice(prev);

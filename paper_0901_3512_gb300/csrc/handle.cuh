@@ -23,6 +23,7 @@ struct seedcg_handle {
     seedcg::DevBuf work;          // working vectors of the solve
     seedcg::DevBuf coef;          // projection coefficients / gemm split scratch
     seedcg::DevBuf staging;       // complex128 staging of host B / X
+    seedcg::DevBuf tcbuf;         // tensor-core projection: bf16 B operand + FP32 partials
     std::vector<double> alpha, beta, delta;  // Lanczos scalars of the last solve
     int last_m = 0;
     std::string err;
@@ -30,6 +31,8 @@ struct seedcg_handle {
 };
 
 namespace seedcg {
+seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const double* X,
+                                 double* C, int use_tc, cudaStream_t st);
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
                          int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st);
 }

@@ -10,6 +10,8 @@
 // type of the precision mode (double2, float2 or bf16x2 per complex entry).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -38,7 +40,13 @@ struct Error {
         }                                                                                  \
     } while (0)
 
-#define SEEDCG_CHECK_LAUNCH() SEEDCG_CUDA_TRY(cudaGetLastError())
+// every kernel launch site ends with this: it checks the launch and counts it
+extern std::atomic<unsigned long long> g_kernel_launches;
+#define SEEDCG_CHECK_LAUNCH()                                                              \
+    do {                                                                                   \
+        ::seedcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);               \
+        SEEDCG_CUDA_TRY(cudaGetLastError());                                               \
+    } while (0)
 
 // ----------------------------------------------------------------------------
 // complex helpers on CUDA vector types

@@ -15,7 +15,10 @@
 #include "handle.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
+#include "tc_proj.cuh"
 #include "wilson.cuh"
+
+#include <type_traits>
 
 namespace seedcg {
 
@@ -271,7 +274,17 @@ k_po_sub(const VT* __restrict__ V, long ldv, int na, const double2* __restrict__
         }
     }
     double red[1] = {(double)part};
-    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) { L.ctl->nv = sqrt(tot[0]); });
+    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) {
+        const double nv = sqrt(tot[0]);
+        L.ctl->nv = nv;
+        // v_i is a unit vector; if the projection removed most of it the basis no
+        // longer spans what the recurrence assumes (numerical invariant subspace or
+        // a basis stored too coarsely): end the run at i - 1, before this vector.
+        if (!(nv >= 0.5)) {
+            L.ctl->breakdown = 2;
+            L.ctl->m = i - 1;
+        }
+    });
 }
 
 // v_i /= ||v_i||; dvf = v_i^dag f
@@ -310,8 +323,16 @@ k_po_finish(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int 
     }
     double red[1] = {(double)part};
     grid_sum<1>(red, L.partials, L.counters + CTR_PO4, [&](double* tot) {
-        L.beta[i - 1] = sqrt(tot[0]);
+        const double bnew = sqrt(tot[0]);
         L.ctl->po_count += 1;
+        // an orthogonal projection never lengthens f; growth means the stored
+        // basis is far from orthonormal: end the run at i - 1
+        if (!(bnew <= 1.01 * L.beta[i - 1])) {
+            L.ctl->breakdown = 3;
+            L.ctl->m = i - 1;
+            return;
+        }
+        L.beta[i - 1] = bnew;
         lz_after_beta(L, i);
     });
 }
@@ -740,6 +761,33 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 
     // pinned host scratch: [0,256) slot lists / flags, [256,512) system lists,
     // [512,1024) active flags, [1024] a zero, doubles from int 2048 on
+    // tensor-core projections for the bf16 basis
+    constexpr bool kBf16 = std::is_same<VT, __nv_bfloat162>::value;
+    const bool use_tc = kBf16 && o.use_tensor_cores;
+    __nv_bfloat162* Bm = nullptr;
+    float* tpart = nullptr;
+    const size_t tpart_elems = (size_t)4 << 20;
+    if (use_tc) {
+        const size_t bb = tc_b_bytes(n, std::min(std::max(nrhs, 2), 32));
+        const size_t need_tc = ((bb + 1023) & ~(size_t)1023) + tpart_elems * sizeof(float);
+        if (h->tcbuf.bytes < need_tc) {
+            h->tcbuf.ensure(need_tc);
+            SEEDCG_CUDA_TRY(cudaMemsetAsync(h->tcbuf.p, 0, need_tc, st));
+        }
+        Bm = h->tcbuf.as<__nv_bfloat162>();
+        tpart = reinterpret_cast<float*>(h->tcbuf.as<char>() + ((bb + 1023) & ~(size_t)1023));
+    }
+    auto project = [&](int rows, const cx_t<R>* X, int nvec, int ldc) {
+        if constexpr (kBf16) {
+            if (use_tc && nvec <= 32) {
+                tc_project(Vb, m_max, rows, reinterpret_cast<const float2*>(X), n, nvec, n, Bm, tpart,
+                           tpart_elems, Cc, ldc, &L.ctl->status, st);
+                return;
+            }
+        }
+        gemm_t<R, VT>(Vb, n, rows, X, n, nvec, n, Cc, ldc, split, split_elems, st);
+    };
+
     int* pin = reinterpret_cast<int*>(h->pinned);
     double* pind = reinterpret_cast<double*>(pin + 2048);
     pin[1024] = 0;
@@ -823,7 +871,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
                 const cx_t<R>* Bst = (v == vA) ? vA : fv;  // rows [v, f] or [f, v]
                 const int cvcol = (v == vA) ? 0 : 1;
                 for (int pass = 0; pass < std::max(o.po_passes, 1); pass++) {
-                    gemm_t<R, VT>(Vb, n, na, Bst, n, 2, n, Cc, 2, split, split_elems, st);
+                    project(na, Bst, 2, 2);
                     k_po_sub<R, VT><<<rb, kRedThreads, 0, st>>>(Vb, n, na, Cc, cvcol, v, fv, n, i, L);
                     SEEDCG_CHECK_LAUNCH();
                 }
@@ -841,7 +889,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
             if (i % poll == 0 || i == m_max) {
                 SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, L.ctl, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
                 SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
-                if (i >= pin[0]) break;
+                if (i >= pin[0] || pin[2] != 0) break;
             }
         }
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, L.ctl, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
@@ -876,7 +924,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     // ---------------- phase S: Galerkin seeds, Eq. (1) ----------------
     t_seed.start(st);
     if (!literal && m > 0) {
-        gemm_t<R, VT>(Vb, n, m, R0, n, nrhs, n, Cc, nrhs, split, split_elems, st);
+        project(m, R0, nrhs, nrhs);
         k_seed_tridiag<<<(nrhs + 63) / 64, 64, 0, st>>>(Cc, nrhs, nrhs, m, L);
         SEEDCG_CHECK_LAUNCH();
         gemm_n<R, VT, double2>(Vb, n, m, Cc, nrhs, nrhs, X64, n, n, 1.0, st);
@@ -1024,6 +1072,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
         SEEDCG_CUDA_TRY(cudaMemcpy(tr.data(), tr_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
     seedcg_status code = SEEDCG_OK;
     if (lz_status == SEEDCG_ERR_NAN) code = SEEDCG_ERR_NAN;
+    else if (lz_status == SEEDCG_ERR_TIMEOUT) code = SEEDCG_ERR_TIMEOUT;
     else if (lz_status == SEEDCG_ERR_BREAKDOWN) code = SEEDCG_ERR_BREAKDOWN;
     if (!o.stop_after_seed && code == SEEDCG_OK) {
         for (int j = 0; j < nrhs; j++)
@@ -1053,6 +1102,53 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 }
 
 }  // namespace
+
+seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const double* X,
+                                 double* C, int use_tc, cudaStream_t st) {
+    const int vol = h->g.vol;
+    const long n = 12L * vol;
+    const int prec = h->vbasis_prec;
+    DevBuf xb, cb, scr;
+    const size_t cbytes = (size_t)rows * nvec * sizeof(double2);
+    cb.ensure(cbytes + 256);
+    const size_t split_elems = std::max<size_t>((size_t)rows * nvec * 64, (size_t)1 << 20);
+    scr.ensure(split_elems * sizeof(double2));
+    if (prec == SEEDCG_FP64) {
+        xb.ensure((size_t)nvec * n * sizeof(double2));
+        to_internal_f64(X, xb.as<double2>(), vol, nvec, st);
+        gemm_t<double, double2>(h->vbasis.as<double2>(), n, rows, xb.as<double2>(), n, nvec, n,
+                                cb.as<double2>(), nvec, scr.as<double2>(), split_elems, st);
+    } else {
+        xb.ensure((size_t)nvec * n * sizeof(float2));
+        to_internal_f32(X, xb.as<float2>(), vol, nvec, st);
+        if (prec == SEEDCG_MIXED_V32) {
+            gemm_t<float, float2>(h->vbasis.as<float2>(), n, rows, xb.as<float2>(), n, nvec, n,
+                                  cb.as<double2>(), nvec, scr.as<double2>(), split_elems, st);
+        } else if (use_tc) {
+            DevBuf bm, part, e;
+            bm.ensure(tc_b_bytes(n, nvec));
+            const size_t pe = (size_t)4 << 20;
+            part.ensure(pe * sizeof(float));
+            e.ensure(sizeof(int));
+            SEEDCG_CUDA_TRY(cudaMemsetAsync(e.p, 0, sizeof(int), st));
+            SEEDCG_CUDA_TRY(cudaMemsetAsync(bm.p, 0, tc_b_bytes(n, nvec), st));
+            tc_project(h->vbasis.as<__nv_bfloat162>(), h->opt.m_max, rows, xb.as<float2>(), n, nvec,
+                       n, bm.as<__nv_bfloat162>(), part.as<float>(), pe, cb.as<double2>(), nvec,
+                       e.as<int>(), st);
+            int herr = 0;
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(&herr, e.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            if (herr) return SEEDCG_ERR_TIMEOUT;
+        } else {
+            gemm_t<float, __nv_bfloat162>(h->vbasis.as<__nv_bfloat162>(), n, rows, xb.as<float2>(), n,
+                                          nvec, n, cb.as<double2>(), nvec, scr.as<double2>(),
+                                          split_elems, st);
+        }
+    }
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(C, cb.p, cbytes, cudaMemcpyDeviceToHost, st));
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SEEDCG_OK;
+}
 
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
                          int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {

@@ -1,0 +1,383 @@
+// Tensor-core projection against the stored basis (bf16 V), sm_103a:
+//
+//   C = V^dag X   for a few complex vectors X (the re-orthogonalisation's
+//                 [v_i, f] of Algorithm 1 step 8, or R_0 for the Eq. (1) seeds)
+//
+// as a real GEMM  D[a][c] = sum_k A[a][k] B[c][k]  with
+//   A = V viewed as bf16 [rows][K = 2N] (each basis vector one row, re/im interleaved),
+//   B = [Re-column, Im-column] per complex vector x: (xr, xi) and (xi, -xr) interleaved,
+//       rounded to bf16, so that D[a][2j] = Re(v_a^dag x_j), D[a][2j+1] = Im(v_a^dag x_j).
+// One CTA owns 128 rows of V and a range of K (split-K); TMA streams 128x64
+// tiles of V and NBx64 tiles of B into a 6-stage shared-memory ring (128-byte
+// swizzle); one thread issues tcgen05.mma (M=128, N=NB, K=16, bf16 -> fp32)
+// into a TMEM accumulator; after the K range four warps read the 128 x NB
+// accumulator back with tcgen05.ld and write FP32 partials, which a second
+// kernel sums over the splits in FP64 (fixed order: deterministic).
+//
+// Every wait on an mbarrier is bounded (1 s of globaltimer); on expiry the
+// kernel records an error code, stops issuing work, waits (bounded) for the
+// copies it already issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.cuh"
+#include "reduce.cuh"
+#include "tc_proj.cuh"
+
+#include <algorithm>
+
+namespace seedcg {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;          // bf16 elements per 128-byte swizzle row
+constexpr int STAGES = 6;
+constexpr uint32_t A_STAGE_BYTES = BM * BK * 2;  // 16 KB
+constexpr unsigned long long WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait: false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > WAIT_NS) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y),
+          "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                           // SWIZZLE_128B
+    return d;
+}
+// instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+template <int NB>
+struct TcSmem {
+    static constexpr uint32_t B_STAGE = ((NB * BK * 2) + 1023) & ~1023u;
+    static constexpr uint32_t BYTES = STAGES * (A_STAGE_BYTES + B_STAGE) + 1024 + 256;
+};
+
+// NB: columns of B (multiple of 16, <= 64).  part: float [nsplit][rows_valid][NB]
+template <int NB>
+__global__ void __launch_bounds__(128, 1)
+k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          int nkb, int kb_per_split, int rows_valid, float* __restrict__ part,
+          int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~(uintptr_t)1023);
+    constexpr uint32_t B_STAGE = TcSmem<NB>::B_STAGE;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_STAGE_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kb0 = blockIdx.y * kb_per_split;
+    const int kb1 = min(kb0 + kb_per_split, nkb);
+    const int nk = kb1 > kb0 ? kb1 - kb0 : 0;
+    constexpr uint32_t TMEM_COLS = NB <= 32 ? 32 : 64;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem_d = *tmem_slot;
+
+    int issued = 0;  // TMA stages issued by the producer
+    if (nk > 0) {
+        if (warp == 0 && lane == 0) {
+            // producer: TMA loads of V and B tiles
+            for (int it = 0; it < nk; it++) {
+                const int s = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u) || *s_fail) {
+                    *s_fail = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], A_STAGE_BYTES + NB * BK * 2);
+                const int x = (kb0 + it) * BK;
+                tma_load_2d(sA + s * A_STAGE_BYTES, &tmA, &full[s], x, blockIdx.x * BM);
+                tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], x, 0);
+                issued = it + 1;
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer
+            constexpr uint32_t idesc = umma_idesc_bf16(NB);
+            for (int it = 0; it < nk; it++) {
+                const int s = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph) || *s_fail) {
+                    *s_fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + s * A_STAGE_BYTES);
+                const uint32_t b0 = smem_u32(sB + s * B_STAGE);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; kk++) {
+                    const uint64_t da = umma_desc_sw128(a0 + kk * 32);
+                    const uint64_t db = umma_desc_sw128(b0 + kk * 32);
+                    umma_bf16(tmem_d, da, db, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                }
+                umma_commit(&empty[s]);
+            }
+            umma_commit(done);
+        }
+        // everyone waits for the accumulator (bounded)
+        if (!mbar_wait(done, 0)) *s_fail = 1;
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool failed = *s_fail != 0;
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(err, SEEDCG_ERR_TIMEOUT);
+        // drain the copies this CTA issued (bounded), so none lands after exit
+        if (warp == 0 && lane == 0) {
+            for (int it = 0; it < issued; it++) {
+                const int s = it % STAGES;
+                mbar_wait(&full[s], (uint32_t)(it / STAGES) & 1u);
+            }
+        }
+    } else {
+        // epilogue: warp w owns TMEM lanes [32w, 32w + 32) = rows of this tile
+        const int row = blockIdx.x * BM + warp * 32 + lane;
+        float* out = part + ((size_t)blockIdx.y * rows_valid + row) * NB;
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+            float v[16];
+            if (nk > 0) {
+                tmem_ld16<NB>(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; k++) v[k] = 0.f;
+            }
+            if (row < rows_valid) {
+#pragma unroll
+                for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4*>(out + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d),
+                     "r"(TMEM_COLS));
+    }
+}
+
+// C[a][j] (complex, double2) = sum over splits of part[split][a][2j] + i part[..][2j+1]
+__global__ void k_tc_reduce(const float* __restrict__ part, int nsplit, int rows, int nb_cols,
+                            int nvec, double2* __restrict__ C, int ldc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * nvec) return;
+    int a = t / nvec, j = t % nvec;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < nsplit; p++) {
+        const float* q = part + ((size_t)p * rows + a) * nb_cols;
+        re += q[2 * j];
+        im += q[2 * j + 1];
+    }
+    C[(size_t)a * ldc + j] = make_double2(re, im);
+}
+
+// B[2j][2e..2e+1] = (xr, xi), B[2j+1][2e..2e+1] = (xi, -xr) in bf16, for x_j = X + j*ldx
+__global__ void k_tc_build_b(const float2* __restrict__ X, long ldx, int nvec, long n,
+                             __nv_bfloat162* __restrict__ Bm) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        for (int j = 0; j < nvec; j++) {
+            float2 x = X[(size_t)j * ldx + e];
+            Bm[(size_t)(2 * j) * n + e] = __floats2bfloat162_rn(x.x, x.y);
+            Bm[(size_t)(2 * j + 1) * n + e] = __floats2bfloat162_rn(x.y, -x.x);
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        SEEDCG_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                         cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p)
+            throw Error{SEEDCG_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor map over [rows][k_elems] with a box of [box_rows][64]
+CUtensorMap make_map(const void* base, uint64_t k_elems, uint64_t rows, uint32_t box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {k_elems, rows};
+    cuuint64_t strides[1] = {k_elems * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (strides[0] & 15))
+        throw Error{SEEDCG_ERR_ARG, "tensor map base/stride not 16-byte aligned"};
+    CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{SEEDCG_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
+    return m;
+}
+
+template <int NB>
+void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int rows, long kelems, float* part,
+               size_t part_elems, int* err, int* nsplit_out, cudaStream_t st) {
+    const int nkb = (int)((kelems + BK - 1) / BK);
+    const int tiles = (rows + BM - 1) / BM;
+    // ~2 CTAs per SM on 152 SMs; every CTA keeps >= 16 K-blocks of work
+    int want = (304 + tiles - 1) / tiles;
+    int maxs = nkb / 16 > 0 ? nkb / 16 : 1;
+    int nsplit = want < maxs ? want : maxs;
+    long cap = (long)(part_elems / ((size_t)rows * NB));
+    if (nsplit > cap) nsplit = (int)cap;
+    if (nsplit < 1) throw Error{SEEDCG_ERR_OOM, "tensor-core projection: partial buffer too small"};
+    int per = (nkb + nsplit - 1) / nsplit;
+    nsplit = (nkb + per - 1) / per;
+    const uint32_t smem = TcSmem<NB>::BYTES;
+    static bool attr_set = false;
+    if (!attr_set) {
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_proj<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    dim3 grid(tiles, nsplit);
+    k_tc_proj<NB><<<grid, 128, smem, st>>>(ma, mb, nkb, per, rows, part, err);
+    SEEDCG_CHECK_LAUNCH();
+    *nsplit_out = nsplit;
+}
+
+}  // namespace
+
+size_t tc_b_bytes(long n, int nvec) {
+    int nb = tc_cols(nvec);
+    return (size_t)nb * n * sizeof(__nv_bfloat162);
+}
+
+int tc_cols(int nvec) {
+    int c = 2 * nvec;
+    return c <= 16 ? 16 : (c <= 32 ? 32 : (c <= 48 ? 48 : 64));
+}
+
+void tc_project(const __nv_bfloat162* V, int rows_alloc, int rows, const float2* X, long ldx,
+                int nvec, long n, __nv_bfloat162* Bm, float* part, size_t part_elems,
+                double2* C, int ldc, int* err, cudaStream_t st) {
+    if (rows <= 0 || nvec <= 0) return;
+    if (nvec > 32) throw Error{SEEDCG_ERR_ARG, "tensor-core projection takes at most 32 vectors"};
+    const int nb = tc_cols(nvec);
+    const long kel = 2 * n;  // bf16 elements per basis vector
+    {
+        int blocks = (int)std::min<long>((n + 255) / 256, 152 * 16);
+        k_tc_build_b<<<blocks, 256, 0, st>>>(X, ldx, nvec, n, Bm);
+        SEEDCG_CHECK_LAUNCH();
+    }
+    CUtensorMap ma = make_map(V, (uint64_t)kel, (uint64_t)rows_alloc, BM);
+    CUtensorMap mb = make_map(Bm, (uint64_t)kel, (uint64_t)nb, (uint32_t)nb);
+    int nsplit = 0;
+    switch (nb) {
+        case 16: launch_tc<16>(ma, mb, rows, kel, part, part_elems, err, &nsplit, st); break;
+        case 32: launch_tc<32>(ma, mb, rows, kel, part, part_elems, err, &nsplit, st); break;
+        case 48: launch_tc<48>(ma, mb, rows, kel, part, part_elems, err, &nsplit, st); break;
+        default: launch_tc<64>(ma, mb, rows, kel, part, part_elems, err, &nsplit, st); break;
+    }
+    const int tot = rows * nvec;
+    k_tc_reduce<<<(tot + 255) / 256, 256, 0, st>>>(part, nsplit, rows, nb, nvec, C, ldc);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+}  // namespace seedcg

@@ -38,7 +38,8 @@ class seedcg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("reliable_delta", ctypes.c_double),
                 ("po_passes", ctypes.c_int), ("seed_mode", ctypes.c_int),
                 ("x0_given", ctypes.c_int), ("cg_maxiter", ctypes.c_int),
-                ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int)]
+                ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int),
+                ("use_tensor_cores", ctypes.c_int)]
 
 
 class seedcg_info(ctypes.Structure):
@@ -56,7 +57,8 @@ _lib = None
 # every entry point of include/seedcg.h, for the export check
 EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "seedcg_solve",
            "seedcg_apply", "seedcg_get_lanczos", "seedcg_get_basis", "seedcg_last_error",
-           "seedcg_destroy"]
+           "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
+           "seedcg_project_basis"]
 
 
 def library_path() -> str:
@@ -88,6 +90,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.seedcg_get_basis.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     lib.seedcg_last_error.argtypes = [vp]
     lib.seedcg_last_error.restype = ctypes.c_char_p
+    lib.seedcg_time_dslash.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_float), vp]
+    lib.seedcg_time_dslash.restype = ctypes.c_int
+    lib.seedcg_project_basis.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
+    lib.seedcg_project_basis.restype = ctypes.c_int
+    lib.seedcg_kernel_launches.argtypes = []
+    lib.seedcg_kernel_launches.restype = ctypes.c_ulonglong
     lib.seedcg_destroy.argtypes = [vp]
     lib.seedcg_destroy.restype = None
     for name in ("seedcg_create", "seedcg_set_options", "seedcg_solve", "seedcg_apply",
@@ -198,6 +207,26 @@ def seedcg_get_basis(h, first: int, count: int, out):
     _check(h, load().seedcg_get_basis(h, int(first), int(count), ctypes.c_void_p(_ptr(out))))
 
 
+def seedcg_time_dslash(h, prec: int, n: int, reps: int, flush_l2: int = 1, stream=None) -> float:
+    ms = ctypes.c_float()
+    _check(h, load().seedcg_time_dslash(h, int(prec), int(n), int(reps), int(flush_l2),
+                                        ctypes.byref(ms), _stream_ptr(stream)))
+    return float(ms.value)
+
+
+def seedcg_project_basis(h, rows: int, nvec: int, X, use_tensor_cores: int = 1, stream=None):
+    """C[a][j] = v_a^dag x_j against the stored basis; returns complex128 [rows][nvec]."""
+    C = np.zeros((rows, nvec), dtype=np.complex128)
+    _check(h, load().seedcg_project_basis(h, int(rows), int(nvec), ctypes.c_void_p(_ptr(X)),
+                                          ctypes.c_void_p(C.ctypes.data), int(use_tensor_cores),
+                                          _stream_ptr(stream)))
+    return C
+
+
+def seedcg_kernel_launches() -> int:
+    return int(load().seedcg_kernel_launches())
+
+
 def seedcg_destroy(h):
     if h:
         load().seedcg_destroy(h)
@@ -235,6 +264,9 @@ class Solver:
     def apply(self, op, inp, out, prec=0, multi=0, stream=None):
         n = inp.shape[0] if len(inp.shape) == 4 else 1
         seedcg_apply(self.h, op, prec, multi, n, inp, out, stream)
+
+    def time_dslash(self, prec=1, n=12, reps=20, flush_l2=1, stream=None):
+        return seedcg_time_dslash(self.h, prec, n, reps, flush_l2, stream)
 
     def close(self):
         if self.h:

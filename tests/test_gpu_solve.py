@@ -115,6 +115,10 @@ def test_tiny_mixed_meets_residual_bar(precision):
         assert tr <= TOL
         assert rel(got[j], Xd[j]) <= cond * TOL
     assert info["reliable_updates"] >= len(eta)
+    if precision == "mixed_vbf16":
+        # on 3072 unknowns a bf16 basis cannot hold PO's orthogonality past
+        # convergence; the run must end Lanczos early and still converge by CG
+        assert info["m"] <= int(np.ceil(wl.past_factor * info["m_conv"]))
     s.close()
 
 
@@ -145,7 +149,8 @@ def test_edge_cases_ragged_lattice():
     for j in (1, 2):
         assert np.linalg.norm(B[j] - op.M(got[j])) <= TOL * np.linalg.norm(B[j])
     # x0 given (a perturbed solution): r0 = b - M x0
-    Xs = np.stack([np.linalg.solve(op.dense(WilsonOperator.OP_M), b.reshape(-1)) for b in B])
+    from oracle.seedcg import cg
+    Xs = np.stack([cg(op.M, b.reshape(-1), None, 1e-12, 20000).x for b in B])
     X0 = (Xs * (1 + 1e-3)).reshape(B.shape)
     s.set_options(past_factor=1.2, x0_given=1)
     X = dev(X0)
