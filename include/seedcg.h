@@ -126,6 +126,23 @@ seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* 
                            void* stream);
 
 /*
+ * Several gauge fields at once (each handle one field, e.g. lattices of
+ * different sizes): for every field, Algorithm 1 on its first right-hand side
+ * and the Eq. (1) seeds of its others; then ONE batched CG over the seeded
+ * systems of all fields (a multi-field multi-RHS dslash per half-step, the
+ * iteration chunks replayed as a CUDA graph).  hs: nfields (1..16) distinct
+ * handles of the same precision mode and device; nrhs[f], B[f], X[f] as in
+ * seedcg_solve for field f (host or device; at most 512 systems in total).
+ * infos: NULL or nfields entries.  The options of each handle apply to its
+ * Lanczos run; those of hs[0] to the CG phase.
+ */
+seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrhs,
+                                 const double* const* B, double* const* X, double tol,
+                                 int extra_iters, int reorth_period, seedcg_info* infos,
+                                 void* stream);
+
+/*
+ * Apply the operator to n spinor fields/*
  * Apply the operator to n spinor fields (for parity checks and for forming
  * b = D^dag eta).  op: 0 = D, 1 = D^dag, 2 = M = D^dag D.  prec: 0 = FP64
  * arithmetic, 1 = FP32 arithmetic (inputs rounded to FP32, result widened).

@@ -4,6 +4,7 @@
 // message kept in the handle.
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "handle.cuh"
 #include "kernels.cuh"
@@ -169,6 +170,66 @@ seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* 
         return code;
     } catch (const Error& e) {
         return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrhs,
+                                 const double* const* B, double* const* X, double tol,
+                                 int extra_iters, int reorth_period, seedcg_info* infos,
+                                 void* stream) {
+    if (!hs || nfields < 1 || nfields > 16 || !nrhs || !B || !X)
+        return fail(nullptr, SEEDCG_ERR_ARG, "batch: need 1..16 handles and per-field nrhs, B, X");
+    seedcg_handle* h0 = hs[0];
+    if (!h0) return fail(nullptr, SEEDCG_ERR_ARG, "batch: NULL handle");
+    if (!(tol > 0.0) || !(tol < 1.0)) return fail(h0, SEEDCG_ERR_ARG, "tol must be in (0, 1)");
+    if (extra_iters < 0 || reorth_period < 0)
+        return fail(h0, SEEDCG_ERR_ARG, "extra_iters and reorth_period must be >= 0");
+    int total = 0;
+    for (int f = 0; f < nfields; f++) {
+        if (!hs[f] || !B[f] || !X[f]) return fail(h0, SEEDCG_ERR_ARG, "batch: NULL handle, B or X");
+        if (nrhs[f] < 1 || nrhs[f] > 256) return fail(h0, SEEDCG_ERR_ARG, "batch: nrhs must be in [1, 256]");
+        if (hs[f]->opt.precision != h0->opt.precision || hs[f]->device != h0->device)
+            return fail(h0, SEEDCG_ERR_ARG, "batch: all handles need the same precision and device");
+        for (int g = 0; g < f; g++)
+            if (hs[g] == hs[f]) return fail(h0, SEEDCG_ERR_ARG, "batch: a handle appears twice");
+        total += nrhs[f];
+    }
+    if (total > 512) return fail(h0, SEEDCG_ERR_ARG, "batch: at most 512 systems");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h0->device));
+        std::vector<seedcg::DevBuf> hb(nfields), hx(nfields);
+        std::vector<const double*> Bd(nfields);
+        std::vector<double*> Xd(nfields);
+        std::vector<bool> xhost(nfields, false);
+        for (int f = 0; f < nfields; f++) {
+            const size_t bytes = (size_t)nrhs[f] * hs[f]->g.vol * 12 * sizeof(double2);
+            Bd[f] = B[f];
+            Xd[f] = X[f];
+            if (!is_device_ptr(B[f])) {
+                hb[f].ensure(bytes);
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(hb[f].p, B[f], bytes, cudaMemcpyHostToDevice, st));
+                Bd[f] = hb[f].as<double>();
+            }
+            if (!is_device_ptr(X[f])) {
+                xhost[f] = true;
+                hx[f].ensure(bytes);
+                if (hs[f]->opt.x0_given)
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(hx[f].p, X[f], bytes, cudaMemcpyHostToDevice, st));
+                Xd[f] = hx[f].as<double>();
+            }
+        }
+        seedcg_status code = seedcg::batch_solve_impl(hs, nfields, nrhs, Bd.data(), Xd.data(), tol,
+                                                      extra_iters, reorth_period, infos, st);
+        for (int f = 0; f < nfields; f++)
+            if (xhost[f])
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(X[f], Xd[f], (size_t)nrhs[f] * hs[f]->g.vol * 12 * sizeof(double2),
+                                                cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (code != SEEDCG_OK) h0->err = "batch: a system did not converge or a Lanczos run failed";
+        return code;
+    } catch (const Error& e) {
+        return fail(h0, e.code, e.msg);
     }
 }
 
@@ -361,6 +422,7 @@ void seedcg_destroy(seedcg_handle* h) {
     h->work.release();
     h->coef.release();
     h->tcbuf.release();
+    h->cgbuf.release();
     h->staging.release();
     if (h->pinned) cudaFreeHost(h->pinned);
     cudaSetDevice(prev);

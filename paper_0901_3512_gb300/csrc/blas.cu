@@ -122,6 +122,7 @@ k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__
             }
             __syncthreads();
             if (e < n) {
+#pragma unroll 8
                 for (int a = 0; a < cnt; a++) {
                     cx_t<R> av = ld_cx<R>(A, (size_t)(a0 + a) * lda + e);
 #pragma unroll
@@ -140,6 +141,82 @@ k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// proj: the split-K projection C = V^dag X for NV <= 4 vectors, the shape of the
+// re-orthogonalisation (NV = 2: [v_i, f]).  A block owns CHUNK consecutive
+// entries: it stages X there in shared memory once, then its warps sweep the
+// rows of V (RPW rows per pass, coalesced 256-byte row segments), reduce each
+// row with warp shuffles and write one FP64 partial per (block, row, vector).
+// V is read exactly once from HBM.
+// ---------------------------------------------------------------------------
+template <typename R, typename VT, int NV, int RPW, int CHUNK>
+__global__ void __launch_bounds__(256)
+k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __restrict__ X,
+               long ldx, int nv, long n, int chunk, double2* __restrict__ part) {
+    __shared__ cx_t<R> sx[NV][CHUNK];
+    const long e0 = (long)blockIdx.x * chunk;
+    const int cnt = (int)(n - e0 < chunk ? n - e0 : chunk);
+    for (int k = threadIdx.x; k < NV * chunk; k += blockDim.x) {
+        const int j = k / chunk, e = k % chunk;
+        sx[j][e] = (j < nv && e < cnt) ? X[(size_t)j * ldx + e0 + e] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double2* out = part + (size_t)blockIdx.x * na * NV;
+    for (int a0 = warp * RPW; a0 < na; a0 += nw * RPW) {
+        cx_t<R> acc[RPW][NV];
+#pragma unroll
+        for (int r = 0; r < RPW; r++)
+#pragma unroll
+            for (int j = 0; j < NV; j++) acc[r][j] = mk<R>(0, 0);
+        const VT* rows[RPW];
+#pragma unroll
+        for (int r = 0; r < RPW; r++) rows[r] = V + (size_t)(a0 + r < na ? a0 + r : a0) * ldv + e0;
+#pragma unroll 4
+        for (int e = lane; e < cnt; e += 32) {
+            cx_t<R> xv[NV];
+#pragma unroll
+            for (int j = 0; j < NV; j++) xv[j] = sx[j][e];
+#pragma unroll
+            for (int r = 0; r < RPW; r++) {
+                const cx_t<R> a = ld_cx<R>(rows[r], e);
+#pragma unroll
+                for (int j = 0; j < NV; j++) acc[r][j] = cfma_conj(a, xv[j], acc[r][j]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RPW; r++) {
+#pragma unroll
+            for (int j = 0; j < NV; j++) {
+                double re = warp_sum((double)acc[r][j].x);
+                double im = warp_sum((double)acc[r][j].y);
+                if (lane == 0 && a0 + r < na && j < nv)
+                    out[(size_t)(a0 + r) * NV + j] = make_double2(re, im);
+            }
+        }
+    }
+}
+
+// C[a][j] = sum over blocks of part[b][a][j]: one warp per output, lanes stride
+// over the blocks, then a fixed shuffle tree (deterministic)
+template <int NV>
+__global__ void k_proj_reduce(const double2* __restrict__ part, int nblk, int na, int nv,
+                              double2* __restrict__ C, int ldc, int c0) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= na * nv) return;
+    const int a = w / nv, j = w % nv;
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+        const double2 z = part[((size_t)b * na + a) * NV + j];
+        re += z.x;
+        im += z.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) C[(size_t)a * ldc + c0 + j] = make_double2(re, im);
 }
 
 template <typename ST, typename DT>
@@ -185,6 +262,54 @@ void gemm_t(const AT* A, long lda, int na, const cx_t<R>* B, long ldb, int nb, l
     SEEDCG_CHECK_LAUNCH();
 }
 
+// staged entries per block: 32 KB of shared memory for the NV vectors
+template <typename R, int NV> constexpr int proj_chunk() { return 32768 / (NV * (int)sizeof(cx_t<R>)); }
+
+// entries per block: enough blocks to fill 152 SMs twice, at most the staging capacity
+inline int proj_chunk_for(long n, int cap) {
+    long c = (n + 303) / 304;
+    c = (c + 31) / 32 * 32;
+    if (c < 256) c = 256;
+    if (c > cap) c = cap;
+    return (int)c;
+}
+
+template <typename R, typename AT>
+size_t proj_scratch_elems(long n, int na) {
+    const long c2 = proj_chunk_for(n, proj_chunk<R, 2>());
+    const long c4 = proj_chunk_for(n, proj_chunk<R, 4>());
+    const size_t a = (size_t)((n + c2 - 1) / c2) * 2, b = (size_t)((n + c4 - 1) / c4) * 4;
+    return (a > b ? a : b) * (size_t)na;
+}
+
+template <typename R, typename AT>
+void proj(const AT* A, long lda, int na, const cx_t<R>* X, long ldx, int nx, long n, double2* C,
+          int ldc, double2* scratch, size_t scratch_elems, cudaStream_t s) {
+    if (na <= 0 || nx <= 0) return;
+    for (int c0 = 0; c0 < nx; c0 += 4) {
+        const int nv = nx - c0 < 4 ? nx - c0 : 4;
+        const cx_t<R>* Xc = X + (size_t)c0 * ldx;
+        if (nv <= 2) {
+            constexpr int CH = proj_chunk<R, 2>();
+            const int ch = proj_chunk_for(n, CH);
+            const int nblk = (int)((n + ch - 1) / ch);
+            if ((size_t)nblk * na * 2 > scratch_elems) throw Error{SEEDCG_ERR_OOM, "proj scratch"};
+            k_proj_partial<R, AT, 2, 2, CH><<<nblk, 256, 0, s>>>(A, lda, na, Xc, ldx, nv, n, ch, scratch);
+            SEEDCG_CHECK_LAUNCH();
+            k_proj_reduce<2><<<(na * nv + 7) / 8, 256, 0, s>>>(scratch, nblk, na, nv, C, ldc, c0);
+        } else {
+            constexpr int CH = proj_chunk<R, 4>();
+            const int ch = proj_chunk_for(n, CH);
+            const int nblk = (int)((n + ch - 1) / ch);
+            if ((size_t)nblk * na * 4 > scratch_elems) throw Error{SEEDCG_ERR_OOM, "proj scratch"};
+            k_proj_partial<R, AT, 4, 1, CH><<<nblk, 256, 0, s>>>(A, lda, na, Xc, ldx, nv, n, ch, scratch);
+            SEEDCG_CHECK_LAUNCH();
+            k_proj_reduce<4><<<(na * nv + 7) / 8, 256, 0, s>>>(scratch, nblk, na, nv, C, ldc, c0);
+        }
+        SEEDCG_CHECK_LAUNCH();
+    }
+}
+
 template <typename R, typename AT, typename YT>
 void gemm_n(const AT* A, long lda, int na, const double2* C, int ldc, int nb, YT* Y, long ldy,
             long n, double sign, cudaStream_t s) {
@@ -215,6 +340,13 @@ template void dot<float>(const float2*, const float2*, long, double*, unsigned*,
 template void gemm_t<double, double2>(const double2*, long, int, const double2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
 template void gemm_t<float, float2>(const float2*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
 template void gemm_t<float, __nv_bfloat162>(const __nv_bfloat162*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+
+template void proj<double, double2>(const double2*, long, int, const double2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+template void proj<float, float2>(const float2*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+template void proj<float, __nv_bfloat162>(const __nv_bfloat162*, long, int, const float2*, long, int, long, double2*, int, double2*, size_t, cudaStream_t);
+template size_t proj_scratch_elems<double, double2>(long, int);
+template size_t proj_scratch_elems<float, float2>(long, int);
+template size_t proj_scratch_elems<float, __nv_bfloat162>(long, int);
 
 template void gemm_n<double, double2, double2>(const double2*, long, int, const double2*, int, int, double2*, long, long, double, cudaStream_t);
 template void gemm_n<float, float2, float2>(const float2*, long, int, const double2*, int, int, float2*, long, long, double, cudaStream_t);

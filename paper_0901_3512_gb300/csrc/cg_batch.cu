@@ -1,0 +1,685 @@
+// Batched CG engine (the "standard CG" of Section 2 for every seeded system,
+// run for all systems of all gauge fields at once).
+//
+// Every iteration is five launches whatever the number of fields or systems:
+//   1. one multi-field multi-RHS dslash  t = D p   (tiles of 32 sites of every
+//      field; each tile stages its links once, scaled by -kappa and the
+//      boundary sign, and applies them to all of the field's active systems)
+//   2. the same kernel for q = D^dag t, fused with the per-tile share of
+//      Re p^dag q for the step length
+//   3. alpha_j = ||r_j||^2 / p_j^dag q_j          (one block per system)
+//   4. x += alpha p, r -= alpha q, ||r||^2, beta   (rows = systems)
+//   5. p = r + beta p
+// A chunk of `poll` iterations is captured once as a CUDA graph and replayed;
+// the kernels read the active-system tables from device memory, so the graph
+// stays valid while systems converge and are compacted away.  Between chunks
+// the host reads the per-system flags, runs the FP64 reliable updates
+// (x64 += x_R, r = b - M x64 in FP64) and compacts the active systems.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cg_batch.cuh"
+#include "kernels.cuh"
+#include "reduce.cuh"
+#include "wilson.cuh"
+
+namespace seedcg {
+
+namespace {
+
+constexpr int kMaxGroups = 16;
+constexpr int TS = 32;       // sites per dslash tile (one warp per right-hand side)
+constexpr int RPB = 8;       // right-hand sides processed side by side per tile
+
+template <typename R>
+struct GroupDev {
+    Geom g;
+    const cx_t<R>* u;   // links in the working precision
+    R kappa;
+    long n;             // 12 * volume
+    cx_t<R>* xr;        // [cap][n] iterate increments since the last reliable update
+    cx_t<R>* r;
+    cx_t<R>* p;
+    cx_t<R>* q;
+    cx_t<R>* t;
+    double* part;       // [cap][ntiles] shares of p^dag q
+    int ntiles;
+    int tile0;          // first tile of this group in the dslash grid
+    int row0;           // first global row of this group
+};
+
+struct Rows {
+    int* group;   // [rows_cap] group of the row, -1 when unused
+    int* local;   // [rows_cap] system slot within its group
+    int* nact;    // [kMaxGroups] active systems of each group (slots 0..nact-1)
+};
+
+struct CgS {
+    double* rr;
+    double* rr_ru;
+    double* alpha;
+    double* beta;
+    double* bn;
+    int* active;
+    int* flag;      // 0 none, 1 reliable update due, 2 converged (check), 3 stop
+    int* iters;
+    double* partials;
+    unsigned* counters;
+    double tol, delta2;
+    int maxiter;
+};
+
+__device__ __forceinline__ int find_group(int b, int ng, const int* tile0) {
+    int f = 0;
+    while (f + 1 < ng && b >= tile0[f + 1]) f++;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// 1/2: multi-field multi-RHS dslash (DAG = 0: t = D p; DAG = 1: q = D^dag t [+ dot])
+// ---------------------------------------------------------------------------
+template <typename R, int DAG, bool DOT>
+__global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? 3 : 1))
+k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
+    __shared__ cx_t<R> sl[2][4][9][TS];
+    __shared__ int sb[4][TS];
+    __shared__ R sgn[2][TS];
+    __shared__ int s_tile0[kMaxGroups];
+    if (threadIdx.x < ng) s_tile0[threadIdx.x] = G[threadIdx.x].tile0;
+    __syncthreads();
+    const int f = find_group(blockIdx.x, ng, s_tile0);
+    const GroupDev<R>& gd = G[f];
+    const int nsys = rows.nact[f];
+    if (nsys == 0) return;
+    const Geom g = gd.g;
+    const int vol = g.vol;
+    const int tile = blockIdx.x - gd.tile0;
+    const int s0 = tile * TS;
+    const R kappa = gd.kappa;
+    if (threadIdx.x < TS) {
+        const int s = s0 + threadIdx.x;
+        if (s < vol) {
+            Nbr nb = neighbours(g, s);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) sb[mu][threadIdx.x] = nb.b[mu];
+            sgn[0][threadIdx.x] = nb.fwrap_t ? kappa : -kappa;
+            sgn[1][threadIdx.x] = nb.bwrap_t ? kappa : -kappa;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 72 * TS; e += blockDim.x) {
+        const int j = e % TS;
+        const int c = (e / TS) % 9;
+        const int mu = (e / (9 * TS)) % 4;
+        const int dir = e / (36 * TS);
+        const int s = s0 + j;
+        cx_t<R> z = mk<R>(0, 0);
+        if (s < vol) {
+            z = __ldg(gd.u + (size_t)(mu * 9 + c) * vol + (dir ? sb[mu][j] : s));
+            z = cscale(z, mu == 3 ? sgn[dir][j] : -kappa);
+        }
+        sl[dir][mu][c][j] = z;
+    }
+    __syncthreads();
+    const int j = threadIdx.x % TS;   // lane = site of the tile
+    const int qg = threadIdx.x / TS;  // warp = right-hand-side group
+    const int s = s0 + j;
+    const bool live = s < vol;
+    Nbr nb;
+    if (live) nb = neighbours(g, s);
+    auto fl = [&](int mu, int e) { return sl[0][mu][e][j]; };
+    auto bl = [&](int mu, int e) { return sl[1][mu][e][j]; };
+    const cx_t<R>* in = DAG ? gd.t : gd.p;
+    cx_t<R>* out = DAG ? gd.q : gd.t;
+    for (int r = qg; r < nsys; r += RPB) {
+        double d = 0.0;
+        if (live) {
+            const cx_t<R>* inr = in + (size_t)r * gd.n;
+            Spinor<R> res;
+            auto load = [&](int y, Spinor<R>& sp) { load_spinor(inr, vol, y, sp); };
+            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            store_spinor(out + (size_t)r * gd.n, vol, s, res);
+            if (DOT) {
+                const cx_t<R>* pr = gd.p + (size_t)r * gd.n;
+                R acc = 0;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
+                    const cx_t<R> rz = res.c[k / 3][k % 3];
+                    acc += pz.x * rz.x + pz.y * rz.y;
+                }
+                d = (double)acc;
+            }
+        }
+        if (DOT) {
+            d = warp_sum(d);
+            if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
+        }
+    }
+}
+
+// 3: alpha = rr / sum of the tile shares (one block per row, fixed order)
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_mf_alpha(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+    const int row = blockIdx.x;
+    const int f = rows.group[row];
+    if (f < 0 || !C.active[row]) return;
+    const GroupDev<R>& gd = G[f];
+    const double* part = gd.part + (size_t)rows.local[row] * gd.ntiles;
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < gd.ntiles; b += blockDim.x) v[0] += part[b];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) C.alpha[row] = C.rr[row] / v[0];
+}
+
+// per-row grid reduction (grid = (blocks, rows); row = blockIdx.y)
+template <int NV, typename Fin>
+__device__ __forceinline__ void rowsum(double (&v)[NV], double* partials, unsigned* counters,
+                                       Fin fin) {
+    __shared__ bool s_last;
+    block_sum<NV>(v);
+    const unsigned nblk = gridDim.x, row = blockIdx.y;
+    double* part = partials + (size_t)row * NV * nblk;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) part[(size_t)k * nblk + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(counters + row, 1u);
+        s_last = (t == nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) tot[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; k++) tot[k] += __ldcg(part + (size_t)k * nblk + b);
+    block_sum<NV>(tot);
+    if (threadIdx.x == 0) {
+        fin(tot);
+        counters[row] = 0u;
+        __threadfence();
+    }
+}
+
+// 4: x += alpha p, r -= alpha q, ||r||^2, beta and the per-row flags
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_mf_xr(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+    const int row = blockIdx.y;
+    const int f = rows.group[row];
+    if (f < 0 || !C.active[row]) return;
+    const GroupDev<R>& gd = G[f];
+    const size_t off = (size_t)rows.local[row] * gd.n;
+    cx_t<R>* x = gd.xr + off;
+    cx_t<R>* r = gd.r + off;
+    const cx_t<R>* p = gd.p + off;
+    const cx_t<R>* w = gd.q + off;
+    const R a = (R)C.alpha[row];
+    R part = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> pv = p[e], wv = w[e], xv = x[e], rv = r[e];
+        xv.x += a * pv.x; xv.y += a * pv.y;
+        rv.x -= a * wv.x; rv.y -= a * wv.y;
+        x[e] = xv;
+        r[e] = rv;
+        part += rv.x * rv.x + rv.y * rv.y;
+    }
+    double red[1] = {(double)part};
+    rowsum<1>(red, C.partials, C.counters, [&](double* tot) {
+        const double rn = tot[0];
+        C.beta[row] = rn / C.rr[row];
+        C.rr[row] = rn;
+        C.iters[row] += 1;
+        if (!isfinite(rn)) {
+            C.flag[row] = 3;
+            C.active[row] = 0;
+        } else if (sqrt(rn) <= C.tol * C.bn[row]) {
+            C.flag[row] = 2;
+            C.active[row] = 0;
+        } else if (C.iters[row] >= C.maxiter) {
+            C.flag[row] = 3;
+            C.active[row] = 0;
+        } else if (C.delta2 > 0.0 && rn < C.delta2 * C.rr_ru[row]) {
+            C.flag[row] = 1;
+        }
+    });
+}
+
+// 5: p = r + beta p
+template <typename R>
+__global__ void k_mf_p(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+    const int row = blockIdx.y;
+    const int f = rows.group[row];
+    if (f < 0 || !C.active[row]) return;
+    const GroupDev<R>& gd = G[f];
+    const size_t off = (size_t)rows.local[row] * gd.n;
+    const cx_t<R>* r = gd.r + off;
+    cx_t<R>* p = gd.p + off;
+    const R b = (R)C.beta[row];
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> rv = r[e], pv = p[e];
+        pv.x = rv.x + b * pv.x;
+        pv.y = rv.y + b * pv.y;
+        p[e] = pv;
+    }
+}
+
+// reliable update of k = 0..nf-1 systems of one group: x64[sys] += x_R[slot]; x_R = 0;
+// gather x64[sys] into Gx[k]
+template <typename R>
+__global__ void k_mf_ru_flush(const int* __restrict__ slot, const int* __restrict__ sys,
+                              cx_t<R>* __restrict__ XR, double2* __restrict__ X64,
+                              double2* __restrict__ Gx, long n) {
+    const int k = blockIdx.y;
+    cx_t<R>* xr = XR + (size_t)slot[k] * n;
+    double2* x = X64 + (size_t)sys[k] * n;
+    double2* gk = Gx + (size_t)k * n;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> d = xr[e];
+        double2 xv = x[e];
+        xv.x += (double)d.x;
+        xv.y += (double)d.y;
+        x[e] = xv;
+        gk[e] = xv;
+        xr[e] = mk<R>(0, 0);
+    }
+}
+
+// r64 = b - (M x)[k]; r_R[slot] = r64; rr, rr_ru, true residual; active flag
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_mf_ru_resid(const int* __restrict__ row_of, const int* __restrict__ slot,
+              const int* __restrict__ sys, const double2* __restrict__ B64,
+              const double2* __restrict__ MX, cx_t<R>* __restrict__ Rv, long n, CgS C,
+              double* __restrict__ tr_out, double* partials, unsigned* counters) {
+    const int k = blockIdx.y;
+    const int row = row_of[k], q = slot[k], j = sys[k];
+    const double2* b = B64 + (size_t)j * n;
+    const double2* mx = MX + (size_t)k * n;
+    cx_t<R>* r = Rv + (size_t)q * n;
+    double part = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        double2 bv = b[e], mv = mx[e];
+        double rx = bv.x - mv.x, ry = bv.y - mv.y;
+        r[e] = mk<R>((R)rx, (R)ry);
+        part += rx * rx + ry * ry;
+    }
+    double red[1] = {part};
+    rowsum<1>(red, partials, counters, [&](double* tot) {
+        const double rn = tot[0];
+        C.rr[row] = rn;
+        C.rr_ru[row] = rn;
+        C.flag[row] = 0;
+        tr_out[k] = C.bn[row] > 0.0 ? sqrt(rn) / C.bn[row] : 0.0;
+        C.active[row] = (C.bn[row] > 0.0 && sqrt(rn) > C.tol * C.bn[row]) ? 1 : 0;
+    });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_norm_rows(const T* __restrict__ base, long n, double* partials, unsigned* counters,
+            double* out) {
+    const int k = blockIdx.y;
+    const T* x = base + (size_t)k * n;
+    double p = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<double> z = ld_cx<double>(x, e);
+        p += z.x * z.x + z.y * z.y;
+    }
+    double red[1] = {p};
+    rowsum<1>(red, partials, counters, [&](double* tot) { out[k] = sqrt(tot[0]); });
+}
+
+struct Carve2 {
+    char* base;
+    size_t off = 0;
+    template <typename T> T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+template <typename R>
+void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta, int maxiter,
+                int poll, bool use_graph, DevBuf& ws, void* pinned, CgResult& out,
+                cudaStream_t st) {
+    const int ng = (int)groups.size();
+    if (ng < 1 || ng > kMaxGroups) throw Error{SEEDCG_ERR_ARG, "1..16 gauge fields per batch"};
+    const bool fp64 = sizeof(R) == 8;
+    const size_t cxR = sizeof(cx_t<R>);
+    int rows_cap = 0, tiles = 0, nsys_max = 0;
+    long nmax = 0;
+    for (auto& gr : groups) {
+        rows_cap += gr.nsys;
+        tiles += (gr.h->g.vol + TS - 1) / TS;
+        nsys_max = std::max(nsys_max, gr.nsys);
+        nmax = std::max(nmax, 12L * gr.h->g.vol);
+    }
+    if (rows_cap > 512) throw Error{SEEDCG_ERR_ARG, "at most 512 systems per batch"};
+    const int rblocks = (int)std::min<long>((nmax + kRedThreads * 4 - 1) / (kRedThreads * 4), 152 * 8);
+
+    // ---- workspace ----
+    size_t need = 1 << 16;
+    auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    for (auto& gr : groups) {
+        const long n = 12L * gr.h->g.vol;
+        for (int k = 0; k < 5; k++) add((size_t)gr.nsys * n * cxR);
+        for (int k = 0; k < 3; k++) add((size_t)gr.nsys * n * sizeof(double2));
+        add((size_t)gr.nsys * ((gr.h->g.vol + TS - 1) / TS) * sizeof(double));
+    }
+    add(sizeof(GroupDev<R>) * kMaxGroups);
+    add(sizeof(double) * 8 * rows_cap + sizeof(int) * 8 * rows_cap);
+    const size_t part_doubles = (size_t)rblocks * (rows_cap + 2) * 2 + 4096;
+    add(part_doubles * sizeof(double));
+    add(sizeof(unsigned) * (rows_cap + 64));
+    ws.ensure(need);
+    Carve2 cv{ws.as<char>()};
+    std::vector<GroupDev<R>> gd(ng);
+    std::vector<double2*> Gx(ng), MX(ng), T64(ng);
+    int tile0 = 0;
+    for (int f = 0; f < ng; f++) {
+        seedcg_handle* h = groups[f].h;
+        const long n = 12L * h->g.vol;
+        const int ns = groups[f].nsys;
+        gd[f].g = h->g;
+        gd[f].u = fp64 ? reinterpret_cast<const cx_t<R>*>(h->u64.p) : reinterpret_cast<const cx_t<R>*>(h->u32.p);
+        gd[f].kappa = (R)h->kappa;
+        gd[f].n = n;
+        gd[f].xr = cv.take<cx_t<R>>((size_t)ns * n);
+        gd[f].r = cv.take<cx_t<R>>((size_t)ns * n);
+        gd[f].p = cv.take<cx_t<R>>((size_t)ns * n);
+        gd[f].q = cv.take<cx_t<R>>((size_t)ns * n);
+        gd[f].t = cv.take<cx_t<R>>((size_t)ns * n);
+        Gx[f] = cv.take<double2>((size_t)ns * n);
+        MX[f] = cv.take<double2>((size_t)ns * n);
+        T64[f] = cv.take<double2>((size_t)ns * n);
+        gd[f].ntiles = (h->g.vol + TS - 1) / TS;
+        gd[f].part = cv.take<double>((size_t)ns * gd[f].ntiles);
+        gd[f].tile0 = tile0;
+        tile0 += gd[f].ntiles;
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(gd[f].xr, 0, (size_t)ns * n * cxR, st));
+    }
+    GroupDev<R>* gdev = cv.take<GroupDev<R>>(kMaxGroups);
+    CgS C;
+    C.rr = cv.take<double>(rows_cap);
+    C.rr_ru = cv.take<double>(rows_cap);
+    C.alpha = cv.take<double>(rows_cap);
+    C.beta = cv.take<double>(rows_cap);
+    C.bn = cv.take<double>(rows_cap);
+    double* trd = cv.take<double>(rows_cap);
+    C.active = cv.take<int>(rows_cap);
+    C.flag = cv.take<int>(rows_cap);
+    C.iters = cv.take<int>(rows_cap);
+    Rows rows;
+    rows.group = cv.take<int>(rows_cap);
+    rows.local = cv.take<int>(rows_cap);
+    rows.nact = cv.take<int>(kMaxGroups);
+    int* ru_row = cv.take<int>(rows_cap);
+    int* ru_slot = cv.take<int>(rows_cap);
+    int* ru_sys = cv.take<int>(rows_cap);
+    C.partials = cv.take<double>(part_doubles);
+    C.counters = cv.take<unsigned>(rows_cap + 64);
+    C.tol = tol;
+    C.delta2 = reliable_delta > 0.0 ? reliable_delta * reliable_delta : 0.0;
+    C.maxiter = maxiter;
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(C.counters, 0, sizeof(unsigned) * (rows_cap + 64), st));
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(C.iters, 0, sizeof(int) * rows_cap, st));
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(C.flag, 0, sizeof(int) * rows_cap, st));
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(gdev, gd.data(), sizeof(GroupDev<R>) * ng, cudaMemcpyHostToDevice, st));
+
+    // pinned host scratch (ints)
+    int* pin = reinterpret_cast<int*>(pinned);
+    double* pind = reinterpret_cast<double*>(pin + 4096);
+
+    // ---- host mirror of the active systems ----
+    std::vector<std::vector<int>> sysmap(ng);   // group -> slot -> system
+    out.iters.assign(ng, {});
+    out.ru.assign(ng, {});
+    out.notconv.assign(ng, {});
+    out.true_resid.assign(ng, {});
+    for (int f = 0; f < ng; f++) {
+        sysmap[f].resize(groups[f].nsys);
+        for (int j = 0; j < groups[f].nsys; j++) sysmap[f][j] = j;
+        out.iters[f].assign(groups[f].nsys, 0);
+        out.ru[f].assign(groups[f].nsys, 0);
+        out.notconv[f].assign(groups[f].nsys, 0);
+        out.true_resid[f].assign(groups[f].nsys, 0.0);
+    }
+    std::vector<int> row0(ng);
+    auto upload_rows = [&]() {
+        // rows in group order, slots 0..nact-1 of each group
+        std::vector<int> rg(rows_cap, -1), rl(rows_cap, 0), na(kMaxGroups, 0);
+        int r = 0;
+        for (int f = 0; f < ng; f++) {
+            row0[f] = r;
+            na[f] = (int)sysmap[f].size();
+            for (int l = 0; l < na[f]; l++, r++) {
+                rg[r] = f;
+                rl[r] = l;
+            }
+        }
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.group, rg.data(), sizeof(int) * rows_cap, cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.local, rl.data(), sizeof(int) * rows_cap, cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.nact, na.data(), sizeof(int) * kMaxGroups, cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        return r;
+    };
+    int nrows = upload_rows();
+
+    // ||b|| per system
+    for (int f = 0; f < ng; f++) {
+        const long n = gd[f].n;
+        dim3 gr(rblocks, groups[f].nsys);
+        k_norm_rows<double2><<<gr, kRedThreads, 0, st>>>(groups[f].b64, n, C.partials, C.counters,
+                                                          C.bn + row0[f]);
+        SEEDCG_CHECK_LAUNCH();
+    }
+
+    // reliable update of a set of rows (grouped by field); returns nothing,
+    // leaves the new active flags in pin[2048..]
+    auto reliable = [&](const std::vector<int>& rset) {
+        std::vector<std::vector<int>> byg(ng);
+        for (int r : rset) {
+            int f = 0;
+            while (f + 1 < ng && r >= row0[f + 1]) f++;
+            byg[f].push_back(r);
+        }
+        for (int f = 0; f < ng; f++) {
+            const int nf = (int)byg[f].size();
+            if (!nf) continue;
+            const long n = gd[f].n;
+            seedcg_handle* h = groups[f].h;
+            for (int k = 0; k < nf; k++) {
+                const int r = byg[f][k], l = r - row0[f];
+                pin[k] = r;
+                pin[512 + k] = l;
+                pin[1024 + k] = sysmap[f][l];
+            }
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_row, pin, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_slot, pin + 512, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_sys, pin + 1024, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+            dim3 gr(rblocks, nf);
+            k_mf_ru_flush<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, gd[f].xr, groups[f].x64, Gx[f], n);
+            SEEDCG_CHECK_LAUNCH();
+            dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, nf, Gx[f], T64[f], st);
+            dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, nf, T64[f], MX[f], st);
+            k_mf_ru_resid<R><<<gr, kRedThreads, 0, st>>>(ru_row, ru_slot, ru_sys, groups[f].b64, MX[f],
+                                                         gd[f].r, n, C, trd, C.partials, C.counters);
+            SEEDCG_CHECK_LAUNCH();
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(pind, trd, sizeof(double) * nf, cudaMemcpyDeviceToHost, st));
+            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+            for (int k = 0; k < nf; k++) {
+                const int l = byg[f][k] - row0[f];
+                out.true_resid[f][sysmap[f][l]] = pind[k];
+                out.ru[f][sysmap[f][l]] += 1;
+                out.reliable_updates++;
+            }
+        }
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin + 2048, C.active, sizeof(int) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    };
+
+    // compact: keep the active rows of every group at the front of its slots
+    auto compact = [&](const std::vector<int>& act) {
+        std::vector<double> rr(rows_cap), rru(rows_cap), bn(rows_cap);
+        std::vector<int> it(rows_cap);
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rr.data(), C.rr, sizeof(double) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rru.data(), C.rr_ru, sizeof(double) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(bn.data(), C.bn, sizeof(double) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(it.data(), C.iters, sizeof(int) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<double> nrr, nru, nbn;
+        std::vector<std::vector<int>> nmap(ng);
+        for (int f = 0; f < ng; f++) {
+            const long n = gd[f].n;
+            int k = 0;
+            for (int l = 0; l < (int)sysmap[f].size(); l++) {
+                const int r = row0[f] + l;
+                out.iters[f][sysmap[f][l]] += it[r];
+                if (!act[r]) continue;
+                if (l != k) {
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(gd[f].xr + (size_t)k * n, gd[f].xr + (size_t)l * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(gd[f].r + (size_t)k * n, gd[f].r + (size_t)l * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(gd[f].p + (size_t)k * n, gd[f].p + (size_t)l * n, n * cxR, cudaMemcpyDeviceToDevice, st));
+                }
+                nmap[f].push_back(sysmap[f][l]);
+                nrr.push_back(rr[r]);
+                nru.push_back(rru[r]);
+                nbn.push_back(bn[r]);
+                k++;
+            }
+        }
+        sysmap = nmap;
+        const int nk = (int)nrr.size();
+        std::vector<int> zeros(std::max(nk, 1), 0), ones(std::max(nk, 1), 1);
+        if (nk > 0) {
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr, nrr.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr_ru, nru.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.bn, nbn.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.iters, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.flag, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active, ones.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        }
+        // rows past the active ones are switched off
+        std::vector<int> off(rows_cap, 0);
+        if (rows_cap > nk)
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active + nk, off.data(), sizeof(int) * (rows_cap - nk), cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        return upload_rows();
+    };
+
+    // ---- start: true residual of every seeded guess ----
+    {
+        std::vector<int> all(nrows);
+        for (int r = 0; r < nrows; r++) all[r] = r;
+        reliable(all);
+        for (int f = 0; f < ng; f++)
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(gd[f].p, gd[f].r, (size_t)groups[f].nsys * gd[f].n * cxR,
+                                            cudaMemcpyDeviceToDevice, st));
+        std::vector<int> act(pin + 2048, pin + 2048 + rows_cap);
+        nrows = compact(act);
+    }
+
+    // ---- the iteration chunk (graph-captured) ----
+    const int gx = rblocks;
+    auto chunk = [&](cudaStream_t s) {
+        for (int it = 0; it < poll; it++) {
+            k_mf_dslash<R, 0, false><<<tiles, TS * RPB, 0, s>>>(gdev, ng, rows);
+            SEEDCG_CHECK_LAUNCH();
+            k_mf_dslash<R, 1, true><<<tiles, TS * RPB, 0, s>>>(gdev, ng, rows);
+            SEEDCG_CHECK_LAUNCH();
+            k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
+            SEEDCG_CHECK_LAUNCH();
+            dim3 gr(gx, rows_cap);
+            k_mf_xr<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
+            SEEDCG_CHECK_LAUNCH();
+            k_mf_p<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
+            SEEDCG_CHECK_LAUNCH();
+        }
+    };
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cs = nullptr;
+    if (use_graph && nrows > 0) {
+        SEEDCG_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        const unsigned long long before = g_kernel_launches.load();
+        SEEDCG_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        chunk(cs);
+        SEEDCG_CUDA_TRY(cudaStreamEndCapture(cs, &graph));
+        g_kernel_launches.store(before);  // capturing launches nothing; replays are counted
+        SEEDCG_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
+        SEEDCG_CUDA_TRY(cudaGraphDestroy(graph));
+    }
+    cudaEvent_t ev = nullptr;
+    if (gexec) SEEDCG_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    while (nrows > 0) {
+        if (gexec) {
+            // keep stream order: st -> graph on cs -> st
+            SEEDCG_CUDA_TRY(cudaEventRecord(ev, st));
+            SEEDCG_CUDA_TRY(cudaStreamWaitEvent(cs, ev, 0));
+            SEEDCG_CUDA_TRY(cudaGraphLaunch(gexec, cs));
+            g_kernel_launches.fetch_add((unsigned long long)5 * poll, std::memory_order_relaxed);
+            SEEDCG_CUDA_TRY(cudaEventRecord(ev, cs));
+            SEEDCG_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+            out.graph_chunks++;
+        } else {
+            chunk(st);
+        }
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, C.flag, sizeof(int) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int> flags(pin, pin + rows_cap);
+        // the device counts iterations since the last compaction; enforce the total cap here
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin + 3072, C.iters, sizeof(int) * rows_cap, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int f = 0; f < ng; f++)
+            for (int l = 0; l < (int)sysmap[f].size(); l++) {
+                const int r = row0[f] + l;
+                if (!flags[r] && out.iters[f][sysmap[f][l]] + pin[3072 + r] >= maxiter) flags[r] = 3;
+            }
+        std::vector<int> fl;
+        for (int r = 0; r < nrows; r++)
+            if (flags[r]) fl.push_back(r);
+        if (fl.empty()) continue;
+        reliable(fl);
+        std::vector<int> act(pin + 2048, pin + 2048 + rows_cap);
+        bool changed = false;
+        for (int r : fl) {
+            int f = 0;
+            while (f + 1 < ng && r >= row0[f + 1]) f++;
+            const int l = r - row0[f];
+            if (flags[r] == 3) {
+                out.notconv[f][sysmap[f][l]] = 1;
+                act[r] = 0;
+            } else if (flags[r] == 2 && act[r]) {
+                // the iterated residual converged but the true one did not: restart
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(gd[f].p + (size_t)l * gd[f].n, gd[f].r + (size_t)l * gd[f].n,
+                                                gd[f].n * cxR, cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        for (int r = 0; r < nrows; r++) changed |= !act[r];
+        if (changed) nrows = compact(act);
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+}
+
+template void batched_cg<double>(std::vector<CgGroup>&, double, double, int, int, bool, DevBuf&, void*, CgResult&, cudaStream_t);
+template void batched_cg<float>(std::vector<CgGroup>&, double, double, int, int, bool, DevBuf&, void*, CgResult&, cudaStream_t);
+
+}  // namespace seedcg

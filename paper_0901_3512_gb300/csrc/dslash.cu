@@ -10,6 +10,12 @@ namespace {
 
 constexpr int kThreads = 128;
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 inline int blocks_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
 
 // ---------------------------------------------------------------------------
@@ -21,9 +27,9 @@ __global__ void k_to_internal_f64(const double2* __restrict__ in, double2* __res
     if (t >= (long)vol * n) return;
     int r = (int)(t / vol), s = (int)(t % vol);
     const double2* src = in + ((size_t)r * vol + s) * 12;
-    double2* dst = out + (size_t)r * 12 * vol + s;
+    double2* dst = out + (size_t)r * 12 * vol;
 #pragma unroll
-    for (int k = 0; k < 12; k++) dst[(size_t)k * vol] = src[k];
+    for (int k = 0; k < 12; k++) dst[sidx(k, s, vol)] = src[k];
 }
 
 __global__ void k_from_internal_f64(const double2* __restrict__ in, double2* __restrict__ out,
@@ -31,10 +37,10 @@ __global__ void k_from_internal_f64(const double2* __restrict__ in, double2* __r
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= (long)vol * n) return;
     int r = (int)(t / vol), s = (int)(t % vol);
-    const double2* src = in + (size_t)r * 12 * vol + s;
+    const double2* src = in + (size_t)r * 12 * vol;
     double2* dst = out + ((size_t)r * vol + s) * 12;
 #pragma unroll
-    for (int k = 0; k < 12; k++) dst[k] = src[(size_t)k * vol];
+    for (int k = 0; k < 12; k++) dst[k] = src[sidx(k, s, vol)];
 }
 
 __global__ void k_to_internal_f32(const double2* __restrict__ in, float2* __restrict__ out,
@@ -43,9 +49,9 @@ __global__ void k_to_internal_f32(const double2* __restrict__ in, float2* __rest
     if (t >= (long)vol * n) return;
     int r = (int)(t / vol), s = (int)(t % vol);
     const double2* src = in + ((size_t)r * vol + s) * 12;
-    float2* dst = out + (size_t)r * 12 * vol + s;
+    float2* dst = out + (size_t)r * 12 * vol;
 #pragma unroll
-    for (int k = 0; k < 12; k++) dst[(size_t)k * vol] = make_float2((float)src[k].x, (float)src[k].y);
+    for (int k = 0; k < 12; k++) dst[sidx(k, s, vol)] = make_float2((float)src[k].x, (float)src[k].y);
 }
 
 __global__ void k_from_internal_f32(const float2* __restrict__ in, double2* __restrict__ out,
@@ -53,11 +59,11 @@ __global__ void k_from_internal_f32(const float2* __restrict__ in, double2* __re
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= (long)vol * n) return;
     int r = (int)(t / vol), s = (int)(t % vol);
-    const float2* src = in + (size_t)r * 12 * vol + s;
+    const float2* src = in + (size_t)r * 12 * vol;
     double2* dst = out + ((size_t)r * vol + s) * 12;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-        float2 q = src[(size_t)k * vol];
+        float2 q = src[sidx(k, s, vol)];
         dst[k] = make_double2(q.x, q.y);
     }
 }
@@ -87,13 +93,11 @@ k_dslash(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restri
     if (s >= g.vol) return;
     const int vol = g.vol;
     Nbr n = neighbours(g, s);
-    Spinor<R> acc, self, res;
+    Spinor<R> res;
     auto load = [&](int y, Spinor<R>& p) { load_spinor(in, vol, y, p); };
     auto fl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + s); };
     auto bl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + n.b[mu]); };
-    hopping_sum<DAG, R>(n, load, fl, bl, acc);
-    load_spinor(in, vol, s, self);
-    wilson_combine(self, acc, kappa, res);
+    wilson_site<DAG, R>(n, s, load, fl, bl, kappa, res);
     store_spinor(out, vol, s, res);
 }
 
@@ -104,31 +108,39 @@ k_dslash(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restri
 // blockDim = TS * RPB; thread (site j, group q) handles rhs q, q+RPB, ...
 // ---------------------------------------------------------------------------
 template <typename R, int DAG, int TS>
-__global__ void k_dslash_mrhs(Geom g, const cx_t<R>* __restrict__ u, R kappa, int n,
-                              const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out) {
-    extern __shared__ unsigned char smem_raw[];
-    cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);  // [2][4][9][TS]
+__global__ void __launch_bounds__(384, (sizeof(R) == 4 ? 2 : 1))
+k_dslash_mrhs(Geom g, const cx_t<R>* __restrict__ u, R kappa, int n,
+              const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out) {
+    // links of the tile, already multiplied by -kappa and the t-boundary sign
+    __shared__ cx_t<R> sl[2][4][9][TS];   // [fwd/bwd][mu][3a+b][site]
+    __shared__ int sb[4][TS];              // x - mu for each tile site
+    __shared__ R sgn[2][TS];               // -kappa * sign of the forward / backward t hop
     const int vol = g.vol;
     const int s0 = blockIdx.x * TS;
     const int nthr = blockDim.x;
-    // stage links: entry e = ((dir*4 + mu)*9 + c)*TS + j
+    if (threadIdx.x < TS) {
+        const int s = s0 + threadIdx.x;
+        if (s < vol) {
+            Nbr nb = neighbours(g, s);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) sb[mu][threadIdx.x] = nb.b[mu];
+            sgn[0][threadIdx.x] = nb.fwrap_t ? kappa : -kappa;
+            sgn[1][threadIdx.x] = nb.bwrap_t ? kappa : -kappa;
+        }
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < 2 * 4 * 9 * TS; e += nthr) {
-        int j = e % TS;
-        int rest = e / TS;
-        int c = rest % 9;
-        int mu = (rest / 9) % 4;
-        int dir = rest / 36;
-        int s = s0 + j;
+        const int j = e % TS;
+        const int c = (e / TS) % 9;
+        const int mu = (e / (9 * TS)) % 4;
+        const int dir = e / (36 * TS);
+        const int s = s0 + j;
         cx_t<R> z = mk<R>(0, 0);
         if (s < vol) {
-            int y = s;
-            if (dir) {
-                int cm = (s / g.stride[mu]) % g.L[mu];
-                y = (cm == 0) ? s + (g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
-            }
-            z = __ldg(u + (size_t)(mu * 9 + c) * vol + y);
+            z = __ldg(u + (size_t)(mu * 9 + c) * vol + (dir ? sb[mu][j] : s));
+            z = cscale(z, mu == 3 ? sgn[dir][j] : -kappa);
         }
-        sl[e] = z;
+        sl[dir][mu][c][j] = z;
     }
     __syncthreads();
     const int j = threadIdx.x % TS;
@@ -137,18 +149,156 @@ __global__ void k_dslash_mrhs(Geom g, const cx_t<R>* __restrict__ u, R kappa, in
     const int s = s0 + j;
     if (s >= vol) return;
     Nbr nb = neighbours(g, s);
-    auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TS + j]; };
-    auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TS + j]; };
+    auto fl = [&](int mu, int e) { return sl[0][mu][e][j]; };
+    auto bl = [&](int mu, int e) { return sl[1][mu][e][j]; };
     for (int r = q; r < n; r += rpb) {
         const cx_t<R>* inr = in + (size_t)r * 12 * vol;
         cx_t<R>* outr = out + (size_t)r * 12 * vol;
-        Spinor<R> acc, self, res;
+        Spinor<R> res;
         auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
-        hopping_sum<DAG, R>(nb, load, fl, bl, acc);
-        load_spinor(inr, vol, s, self);
-        wilson_combine(self, acc, kappa, res);
+        wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
         store_spinor(outr, vol, s, res);
     }
+}
+
+// ---------------------------------------------------------------------------
+// multi right-hand side, brick tiling: a block owns a Bx x By x Bz brick of
+// sites at one t (Bx = Lx), so the x, y and z neighbours of most sites are
+// sites of the same block and hit in L1; its links (scaled by -kappa and the
+// boundary sign) are staged once in dynamic shared memory and reused for every
+// right-hand side.  blockDim = TB * rpb, TB = Bx*By*Bz a multiple of 32.
+// ---------------------------------------------------------------------------
+struct Brick {
+    int bx, by, bz, tb;     // brick extents and sites per brick
+    int ny, nz;             // bricks along y and z
+};
+
+template <typename R, int DAG, int TB, bool DOT = false>
+__global__ void __launch_bounds__(384, (sizeof(R) == 4 ? 2 : 1))
+k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
+               const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out,
+               const cx_t<R>* __restrict__ pdot = nullptr, double* __restrict__ part = nullptr) {
+    __shared__ double sdot_w[12];
+    extern __shared__ unsigned char smem_raw[];
+    cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);            // [2][4][9][TB]
+    int* ss = reinterpret_cast<int*>(sl + 72 * TB);                  // [TB] site index
+    int* sbk = ss + TB;                                              // [4][TB] x - mu
+    R* sg = reinterpret_cast<R*>(sbk + 4 * TB);                      // [2][TB]
+    const int vol = g.vol;
+    int b = blockIdx.x;
+    const int iy = b % br.ny; b /= br.ny;
+    const int iz = b % br.nz;
+    const int t = b / br.nz;
+    if (threadIdx.x < TB) {
+        const int j = threadIdx.x;
+        const int x = j % br.bx, dy = (j / br.bx) % br.by, dz = j / (br.bx * br.by);
+        const int s = x + g.stride[1] * (iy * br.by + dy) + g.stride[2] * (iz * br.bz + dz) + g.stride[3] * t;
+        ss[j] = s;
+        Nbr nb = neighbours(g, s);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) sbk[mu * TB + j] = nb.b[mu];
+        sg[j] = nb.fwrap_t ? kappa : -kappa;
+        sg[TB + j] = nb.bwrap_t ? kappa : -kappa;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 72 * TB; e += blockDim.x) {
+        const int j = e % TB;
+        const int c = (e / TB) % 9;
+        const int mu = (e / (9 * TB)) % 4;
+        const int dir = e / (36 * TB);
+        cx_t<R> z = __ldg(u + (size_t)(mu * 9 + c) * vol + (dir ? sbk[mu * TB + j] : ss[j]));
+        sl[e] = cscale(z, mu == 3 ? sg[dir * TB + j] : -kappa);
+    }
+    __syncthreads();
+    const int j = threadIdx.x % TB;
+    const int q = threadIdx.x / TB;
+    const int rpb = blockDim.x / TB;
+    const int s = ss[j];
+    Nbr nb = neighbours(g, s);
+    auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TB + j]; };
+    auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TB + j]; };
+    if constexpr (!DOT) {
+        for (int r = q; r < n; r += rpb) {
+            const cx_t<R>* inr = in + (size_t)r * 12 * vol;
+            cx_t<R>* outr = out + (size_t)r * 12 * vol;
+            Spinor<R> res;
+            auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
+            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            store_spinor(outr, vol, s, res);
+        }
+        return;
+    }
+    const int passes = (n + rpb - 1) / rpb;
+    for (int pass = 0; pass < passes; pass++) {
+        const int r = pass * rpb + q;
+        double d = 0.0;
+        if (r < n) {
+            const cx_t<R>* inr = in + (size_t)r * 12 * vol;
+            cx_t<R>* outr = out + (size_t)r * 12 * vol;
+            Spinor<R> res;
+            auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
+            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            store_spinor(outr, vol, s, res);
+            if (DOT) {
+                // Re p^dag (this result) at this site, for the CG step length
+                const cx_t<R>* pr = pdot + (size_t)r * 12 * vol;
+                R acc = 0;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
+                    const cx_t<R> rz = res.c[k / 3][k % 3];
+                    acc += pz.x * rz.x + pz.y * rz.y;
+                }
+                d = (double)acc;
+            }
+        }
+        if (DOT) {
+            // TB threads (TB/32 whole warps) share r: warp sums, then a fixed-order sum
+            d = warp_sum_d(d);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) sdot_w[threadIdx.x >> 5] = d;
+            __syncthreads();
+            if (threadIdx.x < rpb && pass * rpb + (int)threadIdx.x < n) {
+                double tsum = 0.0;
+                for (int w = 0; w < TB / 32; w++) tsum += sdot_w[threadIdx.x * (TB / 32) + w];
+                part[(size_t)(pass * rpb + threadIdx.x) * gridDim.x + blockIdx.x] = tsum;
+            }
+        }
+    }
+}
+
+int largest_divisor_at_most(int L, int cap) {
+    int best = 1;
+    for (int d = 1; d <= L && d <= cap; d++)
+        if (L % d == 0) best = d;
+    return best;
+}
+
+bool make_brick(const Geom& g, Brick& br) {
+    br.bx = g.L[0];
+    if (br.bx > 64) return false;
+    br.by = largest_divisor_at_most(g.L[1], 64 / br.bx);
+    br.bz = largest_divisor_at_most(g.L[2], 128 / (br.bx * br.by));
+    br.tb = br.bx * br.by * br.bz;
+    br.ny = g.L[1] / br.by;
+    br.nz = g.L[2] / br.bz;
+    return br.tb % 32 == 0 && br.tb <= 128;
+}
+
+// one launch of a brick kernel; the dynamic shared memory limit is raised once
+// per instantiation (each has its own static flag)
+template <typename R, int DAG, int TB, bool DOT>
+void brick_go(int nb, int threads, size_t smem, cudaStream_t st, const Geom& g, const Brick& br,
+              const cx_t<R>* u, R kappa, int n, const cx_t<R>* in, cx_t<R>* out,
+              const cx_t<R>* pdot, double* part) {
+    static bool attr = false;
+    if (!attr) {
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_dslash_brick<R, DAG, TB, DOT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr = true;
+    }
+    k_dslash_brick<R, DAG, TB, DOT><<<nb, threads, smem, st>>>(g, br, u, kappa, n, in, out, pdot, part);
+    SEEDCG_CHECK_LAUNCH();
 }
 
 template <typename R>
@@ -164,17 +314,49 @@ void launch_dslash(const Geom& g, const cx_t<R>* u, R kappa, int dag, const cx_t
 
 template <typename R>
 void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n,
-                        const cx_t<R>* in, cx_t<R>* out, cudaStream_t st) {
+                        const cx_t<R>* in, cx_t<R>* out, cudaStream_t st,
+                        const cx_t<R>* pdot = nullptr, double* part = nullptr,
+                        int* nblocks_out = nullptr) {
     if (n <= 0) return;
+    Brick br;
+    if (make_brick(g, br) && (br.tb == 64 || br.tb == 96 || br.tb == 128)) {
+        const int maxr = 384 / br.tb;
+        const int passes = (n + maxr - 1) / maxr;
+        const int rpb = (n + passes - 1) / passes;
+        const int threads = br.tb * rpb;
+        const size_t smem = (size_t)br.tb * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
+        const int nb = br.ny * br.nz * g.L[3];
+        if (pdot) {
+            if (!dag) throw Error{SEEDCG_ERR_ARG, "fused dot only on the D^dag half"};
+            if (br.tb == 128) brick_go<R, 1, 128, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else if (br.tb == 96) brick_go<R, 1, 96, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 1, 64, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (nblocks_out) *nblocks_out = nb;
+            return;
+        }
+        if (br.tb == 128) {
+            if (dag) brick_go<R, 1, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 0, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+        } else if (br.tb == 96) {
+            if (dag) brick_go<R, 1, 96, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 0, 96, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+        } else {
+            if (dag) brick_go<R, 1, 64, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 0, 64, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+        }
+        return;
+    }
+    if (pdot) throw Error{SEEDCG_ERR_ARG, "fused dot needs a brick-tiled lattice"};
     constexpr int TS = 32;
-    int rpb = n < 8 ? n : 8;
-    int threads = TS * rpb;
-    size_t smem = sizeof(cx_t<R>) * 2 * 4 * 9 * TS;
-    int nb = blocks_for(g.vol, TS);
+    // right-hand sides handled side by side per block: balanced passes of <= 12
+    const int passes = (n + 11) / 12;
+    const int rpb = (n + passes - 1) / passes;
+    const int threads = TS * rpb;
+    const int nb = blocks_for(g.vol, TS);
     if (dag)
-        k_dslash_mrhs<R, 1, TS><<<nb, threads, smem, st>>>(g, u, kappa, n, in, out);
+        k_dslash_mrhs<R, 1, TS><<<nb, threads, 0, st>>>(g, u, kappa, n, in, out);
     else
-        k_dslash_mrhs<R, 0, TS><<<nb, threads, smem, st>>>(g, u, kappa, n, in, out);
+        k_dslash_mrhs<R, 0, TS><<<nb, threads, 0, st>>>(g, u, kappa, n, in, out);
     SEEDCG_CHECK_LAUNCH();
 }
 
@@ -225,6 +407,23 @@ void dslash_mrhs_f64(const Geom& g, const double2* u, double kappa, int dag, int
 void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                      const float2* in, float2* out, cudaStream_t s) {
     launch_dslash_mrhs<float>(g, u, kappa, dag, n, in, out, s);
+}
+bool dslash_dot_supported(const Geom& g) {
+    Brick br;
+    return make_brick(g, br) && (br.tb == 64 || br.tb == 96 || br.tb == 128);
+}
+int dslash_dot_blocks(const Geom& g) {
+    Brick br;
+    make_brick(g, br);
+    return br.ny * br.nz * g.L[3];
+}
+void dslash_mrhs_dot_f64(const Geom& g, const double2* u, double kappa, int n, const double2* in,
+                         double2* out, const double2* p, double* part, cudaStream_t s) {
+    launch_dslash_mrhs<double>(g, u, kappa, 1, n, in, out, s, p, part);
+}
+void dslash_mrhs_dot_f32(const Geom& g, const float2* u, float kappa, int n, const float2* in,
+                         float2* out, const float2* p, double* part, cudaStream_t s) {
+    launch_dslash_mrhs<float>(g, u, kappa, 1, n, in, out, s, p, part);
 }
 
 }  // namespace seedcg

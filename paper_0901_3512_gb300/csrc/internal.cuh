@@ -3,8 +3,10 @@
 // Device data layout (GB300: 32-wide warps, 128-byte lines; every kernel
 // below maps one thread to one lattice site so that neighbouring threads
 // touch neighbouring addresses):
-//   FP64 spinor  double2 [12][V]      element k = 3*spin + colour of site s at [k*V + s]
-//   FP32 spinor  float2  [12][V]     same element order as FP64
+//   spinor       element k = 3*spin + colour (0..11) of site s at flat complex index
+//                ((k/2)*V + s)*2 + k%2: six "pair" planes, each site's two complex
+//                entries of a plane adjacent (one 16-byte load in FP32, 32 bytes in FP64);
+//                the same flat order in FP64 (double2) and FP32 (float2)
 //   links        T2      [4][9][V]    U_mu(x)[a][b] at [(mu*9 + 3a + b)*V + s]
 // A basis vector of V is one spinor in the same flat order, in the storage
 // type of the precision mode (double2, float2 or bf16x2 per complex entry).
@@ -141,5 +143,14 @@ void dslash_mrhs_f64(const Geom& g, const double2* u, double kappa, int dag, int
                      const double2* in, double2* out, cudaStream_t s);
 void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                      const float2* in, float2* out, cudaStream_t s);
+
+// D^dag on n fields fused with the CG step-length dot: part[r][b] receives block
+// b's share of Re p_r^dag (D^dag in_r); needs a brick-tiled lattice
+bool dslash_dot_supported(const Geom& g);
+int dslash_dot_blocks(const Geom& g);
+void dslash_mrhs_dot_f64(const Geom& g, const double2* u, double kappa, int n, const double2* in,
+                         double2* out, const double2* p, double* part, cudaStream_t s);
+void dslash_mrhs_dot_f32(const Geom& g, const float2* u, float kappa, int n, const float2* in,
+                         float2* out, const float2* p, double* part, cudaStream_t s);
 
 }  // namespace seedcg

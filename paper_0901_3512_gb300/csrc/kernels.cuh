@@ -53,6 +53,14 @@ template <typename R, typename AT>
 void gemm_t(const AT* A, long lda, int na, const cx_t<R>* B, long ldb, int nb, long n,
             double2* C, int ldc, double2* scratch, size_t scratch_elems, cudaStream_t s);
 
+// Same product, streaming form for few vectors (the re-orthogonalisation):
+// V read once, X staged per block in shared memory, FP64 partials per block.
+template <typename R, typename AT>
+void proj(const AT* A, long lda, int na, const cx_t<R>* X, long ldx, int nx, long n, double2* C,
+          int ldc, double2* scratch, size_t scratch_elems, cudaStream_t s);
+template <typename R, typename AT>
+size_t proj_scratch_elems(long n, int na);
+
 // Y[b][e] += sign * sum_a A[a][e] C[a][b]  (accumulated in R, added in Y's type)
 template <typename R, typename AT, typename YT>
 void gemm_n(const AT* A, long lda, int na, const double2* C, int ldc, int nb, YT* Y, long ldy,

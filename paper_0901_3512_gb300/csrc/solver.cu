@@ -12,6 +12,7 @@
 #include <cstring>
 #include <vector>
 
+#include "cg_batch.cuh"
 #include "handle.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -84,13 +85,11 @@ k_lz_D(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restrict
     if (s >= g.vol) return;
     const int vol = g.vol;
     Nbr n = neighbours(g, s);
-    Spinor<R> acc, self, res;
+    Spinor<R> res;
     auto load = [&](int y, Spinor<R>& p) { load_spinor(v, vol, y, p); };
     auto fl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + s); };
     auto bl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + n.b[mu]); };
-    hopping_sum<0, R>(n, load, fl, bl, acc);
-    load_spinor(v, vol, s, self);
-    wilson_combine(self, acc, kappa, res);
+    wilson_site<0, R>(n, s, load, fl, bl, kappa, res);
     store_spinor(t, vol, s, res);
 }
 
@@ -108,24 +107,23 @@ k_lz_Ddag(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restr
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < vol) {
         Nbr n = neighbours(g, s);
-        Spinor<R> acc, self, res;
+        Spinor<R> res;
         auto load = [&](int y, Spinor<R>& p) { load_spinor(t, vol, y, p); };
         auto fl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + s); };
         auto bl = [&](int mu, int e) { return __ldg(u + (size_t)(mu * 9 + e) * vol + n.b[mu]); };
-        hopping_sum<1, R>(n, load, fl, bl, acc);
-        load_spinor(t, vol, s, self);
-        wilson_combine(self, acc, kappa, res);
+        wilson_site<1, R>(n, s, load, fl, bl, kappa, res);
         R part = 0;
 #pragma unroll
         for (int k = 0; k < 12; k++) {
             cx_t<R> fv = res.c[k / 3][k % 3];
-            cx_t<R> vv = v[(size_t)k * vol + s];
+            const size_t ix = sidx(k, s, vol);
+            cx_t<R> vv = v[ix];
             if (i > 1) {
-                cx_t<R> pv = vprev[(size_t)k * vol + s];
+                cx_t<R> pv = vprev[ix];
                 fv.x -= bprev * pv.x;
                 fv.y -= bprev * pv.y;
             }
-            f[(size_t)k * vol + s] = fv;
+            f[ix] = fv;
             part += vv.x * fv.x + vv.y * fv.y;
         }
         red[0] = (double)part;
@@ -259,6 +257,7 @@ k_po_sub(const VT* __restrict__ V, long ldv, int na, const double2* __restrict__
             }
             __syncthreads();
             if (e < n) {
+#pragma unroll 8
                 for (int a = 0; a < cnt; a++) {
                     cx_t<R> x = ld_cx<R>(V, (size_t)(a0 + a) * ldv + e);
                     av = cfma(x, sc[a][0], av);
@@ -400,207 +399,11 @@ __global__ void k_seed_tridiag(double2* C, int ldc, int nrhs, int m, LzDev L) {
     }
 }
 
-// ===========================================================================
-// phase B: batched CG.  Slot q works on system sys[q]; R-precision slot vectors
-// are [nslot][n]; FP64 solutions/right-hand sides are indexed by system.
-// ===========================================================================
-struct CgDev {
-    double* rr;       // [nslot] ||r||^2 of the iterated residual
-    double* rr_ru;    // [nslot] ||r||^2 at the last reliable update
-    double* alpha;    // [nslot]
-    double* beta;     // [nslot]
-    double* bn;       // [nslot] ||b||
-    int* active;      // [nslot]
-    int* flag;        // [nslot] 0 none, 1 reliable update due, 2 converged (check), 3 maxiter
-    int* iters;       // [nslot]
-    double* partials; // [nslot][blocks] * 2
-    unsigned* counters;  // [nslot]
-    double tol, delta2;
-    int maxiter;
-};
-
-// grid (blocks, nslot): each row reduces its own sums
-template <int NV, typename Fin>
-__device__ __forceinline__ void row_sum(double (&v)[NV], double* partials, unsigned* counters,
-                                        Fin fin) {
-    __shared__ bool s_last;
-    block_sum<NV>(v);
-    const unsigned nblk = gridDim.x, row = blockIdx.y;
-    double* part = partials + (size_t)row * NV * nblk;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) part[(size_t)k * nblk + blockIdx.x] = v[k];
-        __threadfence();
-        unsigned t = atomicAdd(counters + row, 1u);
-        s_last = (t == nblk - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double tot[NV];
-#pragma unroll
-    for (int k = 0; k < NV; k++) tot[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < NV; k++) tot[k] += __ldcg(part + (size_t)k * nblk + b);
-    block_sum<NV>(tot);
-    if (threadIdx.x == 0) {
-        fin(tot);
-        counters[row] = 0u;
-        __threadfence();
-    }
-}
-
-// alpha_q = rr_q / Re(p_q^dag q_q)
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads)
-k_cg_alpha(const cx_t<R>* __restrict__ P, const cx_t<R>* __restrict__ Q, long n, CgDev C) {
-    const int q = blockIdx.y;
-    if (!C.active[q]) return;
-    const cx_t<R>* p = P + (size_t)q * n;
-    const cx_t<R>* w = Q + (size_t)q * n;
-    R part = 0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> a = p[e], b = w[e];
-        part += a.x * b.x + a.y * b.y;
-    }
-    double red[1] = {(double)part};
-    row_sum<1>(red, C.partials, C.counters, [&](double* tot) { C.alpha[q] = C.rr[q] / tot[0]; });
-}
-
-// x += alpha p; r -= alpha q; rr_new = ||r||^2; beta = rr_new / rr; flags
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads)
-k_cg_xr(cx_t<R>* __restrict__ X, cx_t<R>* __restrict__ Rv, const cx_t<R>* __restrict__ P,
-        const cx_t<R>* __restrict__ Q, long n, CgDev C) {
-    const int q = blockIdx.y;
-    if (!C.active[q]) return;
-    const R a = (R)C.alpha[q];
-    cx_t<R>* x = X + (size_t)q * n;
-    cx_t<R>* r = Rv + (size_t)q * n;
-    const cx_t<R>* p = P + (size_t)q * n;
-    const cx_t<R>* w = Q + (size_t)q * n;
-    R part = 0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> pv = p[e], wv = w[e], xv = x[e], rv = r[e];
-        xv.x += a * pv.x; xv.y += a * pv.y;
-        rv.x -= a * wv.x; rv.y -= a * wv.y;
-        x[e] = xv;
-        r[e] = rv;
-        part += rv.x * rv.x + rv.y * rv.y;
-    }
-    double red[1] = {(double)part};
-    row_sum<1>(red, C.partials, C.counters, [&](double* tot) {
-        const double rn = tot[0];
-        C.beta[q] = rn / C.rr[q];
-        C.rr[q] = rn;
-        C.iters[q] += 1;
-        if (!isfinite(rn)) {
-            C.flag[q] = 3;
-            C.active[q] = 0;
-        } else if (sqrt(rn) <= C.tol * C.bn[q]) {
-            C.flag[q] = 2;
-            C.active[q] = 0;
-        } else if (C.iters[q] >= C.maxiter) {
-            C.flag[q] = 3;
-            C.active[q] = 0;
-        } else if (C.delta2 > 0.0 && rn < C.delta2 * C.rr_ru[q]) {
-            C.flag[q] = 1;
-        }
-    });
-}
-
-// p = r + beta p
-template <typename R>
-__global__ void k_cg_p(const cx_t<R>* __restrict__ Rv, cx_t<R>* __restrict__ P, long n, CgDev C) {
-    const int q = blockIdx.y;
-    if (!C.active[q]) return;
-    const R b = (R)C.beta[q];
-    const cx_t<R>* r = Rv + (size_t)q * n;
-    cx_t<R>* p = P + (size_t)q * n;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> rv = r[e], pv = p[e];
-        pv.x = rv.x + b * pv.x;
-        pv.y = rv.y + b * pv.y;
-        p[e] = pv;
-    }
-}
-
-// reliable update, part 1: x64[sys] += x_R[slot]; x_R[slot] = 0; gather x64[sys] -> G[k]
-template <typename R>
-__global__ void k_ru_flush(const int* __restrict__ slot, const int* __restrict__ sys,
-                           cx_t<R>* __restrict__ XR, double2* __restrict__ X64,
-                           double2* __restrict__ G, long n) {
-    const int k = blockIdx.y;
-    cx_t<R>* xr = XR + (size_t)slot[k] * n;
-    double2* x = X64 + (size_t)sys[k] * n;
-    double2* gk = G + (size_t)k * n;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> d = xr[e];
-        double2 xv = x[e];
-        xv.x += (double)d.x;
-        xv.y += (double)d.y;
-        x[e] = xv;
-        gk[e] = xv;
-        xr[e] = mk<R>(0, 0);
-    }
-}
-
-// reliable update, part 2: r64 = b - (M x)[k]; r_R[slot] = r64; rr = ||r64||^2
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads)
-k_ru_resid(const int* __restrict__ slot, const int* __restrict__ sys,
-           const double2* __restrict__ B64, const double2* __restrict__ MX,
-           cx_t<R>* __restrict__ Rv, long n, CgDev C, double* __restrict__ tr_out,
-           double* partials, unsigned* counters) {
-    const int k = blockIdx.y;
-    const int q = slot[k], j = sys[k];
-    const double2* b = B64 + (size_t)j * n;
-    const double2* mx = MX + (size_t)k * n;
-    cx_t<R>* r = Rv + (size_t)q * n;
-    double part = 0.0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        double2 bv = b[e], mv = mx[e];
-        double rx = bv.x - mv.x, ry = bv.y - mv.y;
-        r[e] = mk<R>((R)rx, (R)ry);
-        part += rx * rx + ry * ry;
-    }
-    double red[1] = {part};
-    row_sum<1>(red, partials, counters, [&](double* tot) {
-        const double rn = tot[0];
-        C.rr[q] = rn;
-        C.rr_ru[q] = rn;
-        C.flag[q] = 0;
-        tr_out[j] = C.bn[q] > 0.0 ? sqrt(rn) / C.bn[q] : 0.0;
-        C.active[q] = (C.bn[q] > 0.0 && sqrt(rn) > C.tol * C.bn[q]) ? 1 : 0;
-    });
-}
-
 // M x for n FP64 fields in internal layout (D then D^dag) via the multi-RHS kernel
 inline void apply_M64(seedcg_handle* h, int n, const double2* x, double2* tmp, double2* out,
                       cudaStream_t st) {
     dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, n, x, tmp, st);
     dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, n, tmp, out, st);
-}
-
-template <typename R>
-inline void apply_M_mrhs(seedcg_handle* h, int n, const cx_t<R>* x, cx_t<R>* tmp, cx_t<R>* out,
-                         cudaStream_t st);
-template <>
-inline void apply_M_mrhs<double>(seedcg_handle* h, int n, const double2* x, double2* tmp,
-                                 double2* out, cudaStream_t st) {
-    apply_M64(h, n, x, tmp, out, st);
-}
-template <>
-inline void apply_M_mrhs<float>(seedcg_handle* h, int n, const float2* x, float2* tmp,
-                                float2* out, cudaStream_t st) {
-    dslash_mrhs_f32(h->g, h->u32.as<float2>(), (float)h->kappa, 0, n, x, tmp, st);
-    dslash_mrhs_f32(h->g, h->u32.as<float2>(), (float)h->kappa, 1, n, tmp, out, st);
 }
 
 // bump allocator over one device buffer
@@ -657,17 +460,10 @@ __global__ void k_resid_init(const double2* __restrict__ b, const double2* __res
 // ===========================================================================
 // host driver, templated on working precision R and basis storage VT
 // ===========================================================================
-struct CgHost {
-    std::vector<int> sys;         // slot -> system
-    std::vector<int> iters;       // per system
-    std::vector<int> ru;          // reliable updates per system
-    std::vector<int> notconv;     // per system
-};
-
 template <typename R, typename VT>
 seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2* X64,
                         double tol, int extra_iters, int k_po, seedcg_info* info,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool run_cg = true) {
     const seedcg_options& o = h->opt;
     const int vol = h->g.vol;
     const long n = 12L * vol;
@@ -721,31 +517,12 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     L.eta = cs.take<double2>(nrhs + 2);
     double* bnorm = cs.take<double>(nrhs + 2);
     double* tr_dev = cs.take<double>(nrhs + 2);
-    // CG scalars
-    CgDev C;
-    C.rr = cs.take<double>(nrhs + 2);
-    C.rr_ru = cs.take<double>(nrhs + 2);
-    C.alpha = cs.take<double>(nrhs + 2);
-    C.beta = cs.take<double>(nrhs + 2);
-    C.bn = cs.take<double>(nrhs + 2);
-    C.active = cs.take<int>(nrhs + 2);
-    C.flag = cs.take<int>(nrhs + 2);
-    C.iters = cs.take<int>(nrhs + 2);
-    int* ru_slot = cs.take<int>(nrhs + 2);
-    int* ru_sys = cs.take<int>(nrhs + 2);
-
     const int rb = red_blocks(n);
     const size_t part_doubles = (size_t)std::max(kMaxRedBlocks, rb * (nrhs + 2)) * 64;
     h->red.ensure(part_doubles * sizeof(double) + 8192 * sizeof(unsigned));
     L.partials = h->red.as<double>();
     L.counters = reinterpret_cast<unsigned*>(h->red.as<double>() + part_doubles);
     SEEDCG_CUDA_TRY(cudaMemsetAsync(L.counters, 0, 8192 * sizeof(unsigned), st));
-    C.partials = L.partials;
-    C.counters = L.counters + 1024;
-    C.tol = tol;
-    C.delta2 = fp64 ? 0.0 : o.reliable_delta * o.reliable_delta;
-    C.maxiter = o.cg_maxiter;
-
     // V basis and coefficient scratch
     const size_t vrow = (size_t)n * sizeof(VT);
     h->vbasis.ensure(vrow * (size_t)m_max);
@@ -754,7 +531,10 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     h->vbasis_m = 0;
     const size_t cols = (size_t)std::max(nrhs, 2);
     const size_t coef_elems = ms * cols;
-    const size_t split_elems = std::max<size_t>(coef_elems * 48, (size_t)1 << 20);
+    const bool seeds_streamed = !fp64 && !(std::is_same<VT, __nv_bfloat162>::value && o.use_tensor_cores);
+    const size_t split_elems = std::max<size_t>(
+        std::max<size_t>(coef_elems * 48, (size_t)1 << 20),
+        seeds_streamed ? proj_scratch_elems<R, VT>(n, m_max) : proj_scratch_elems<R, VT>(n, m_max) / 2);
     h->coef.ensure((coef_elems + split_elems) * sizeof(double2));
     double2* Cc = h->coef.as<double2>();
     double2* split = Cc + coef_elems;
@@ -785,7 +565,10 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
                 return;
             }
         }
-        gemm_t<R, VT>(Vb, n, rows, X, n, nvec, n, Cc, ldc, split, split_elems, st);
+        if (nvec <= 2 || seeds_streamed)
+            proj<R, VT>(Vb, n, rows, X, n, nvec, n, Cc, ldc, split, split_elems, st);
+        else
+            gemm_t<R, VT>(Vb, n, rows, X, n, nvec, n, Cc, ldc, split, split_elems, st);
     };
 
     int* pin = reinterpret_cast<int*>(h->pinned);
@@ -933,164 +716,45 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 
     // ---------------- phase B: batched CG ----------------
     t_cg.start(st);
-    CgHost ch;
-    ch.iters.assign(nrhs, 0);
-    ch.ru.assign(nrhs, 0);
-    ch.notconv.assign(nrhs, 0);
-    int reliable_updates = 0;
-    if (!o.stop_after_seed) {
-        SEEDCG_CUDA_TRY(cudaMemsetAsync(XR, 0, (size_t)nrhs * n * cxR, st));
-        SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.bn, bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, st));
-        // reliable update over a list of (slot, system) pairs
-        auto reliable = [&](const std::vector<int>& slots) {
-            const int nf = (int)slots.size();
-            for (int k = 0; k < nf; k++) {
-                pin[k] = slots[k];
-                pin[256 + k] = ch.sys[slots[k]];
-            }
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_slot, pin, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(ru_sys, pin + 256, sizeof(int) * nf, cudaMemcpyHostToDevice, st));
-            dim3 gr(rb, nf);
-            k_ru_flush<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, XR, X64, G, n);
-            SEEDCG_CHECK_LAUNCH();
-            apply_M64(h, nf, G, T64, MX, st);
-            k_ru_resid<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, B64, MX, Rr, n, C, tr_dev,
-                                                      C.partials, C.counters);
-            SEEDCG_CHECK_LAUNCH();
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin + 512 + 0, C.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
-            for (int k = 0; k < nf; k++) {
-                ch.ru[ch.sys[slots[k]]] += 1;
-                reliable_updates++;
-            }
-        };
-        int nslot = nrhs;
-        ch.sys.resize(nrhs);
-        for (int j = 0; j < nrhs; j++) ch.sys[j] = j;
-        std::vector<int> all(nrhs);
-        for (int j = 0; j < nrhs; j++) all[j] = j;
-        if (nrhs > 256) throw Error{SEEDCG_ERR_ARG, "nrhs > 256 is not supported"};
-        reliable(all);
-        SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv, Rr, (size_t)nrhs * n * cxR, cudaMemcpyDeviceToDevice, st));
-        std::vector<int> act(pin + 512, pin + 512 + nrhs);
-
-        auto compact = [&]() {
-            // download per-slot scalars, keep the active slots in front
-            std::vector<double> hd(5 * nslot);
-            std::vector<int> hi(3 * nslot);
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 0 * nslot, C.rr, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 1 * nslot, C.rr_ru, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hd.data() + 2 * nslot, C.bn, sizeof(double) * nslot, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hi.data() + 0 * nslot, C.iters, sizeof(int) * nslot, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
-            std::vector<int> keep;
-            for (int q = 0; q < nslot; q++) {
-                ch.iters[ch.sys[q]] += hi[q];
-                if (act[q]) keep.push_back(q);
-            }
-            const int nk = (int)keep.size();
-            std::vector<double> nrr(nk), nru(nk), nbn(nk);
-            std::vector<int> nsys(nk), zeros(nk, 0), ones(nk, 1);
-            for (int k = 0; k < nk; k++) {
-                int q = keep[k];
-                nrr[k] = hd[q];
-                nru[k] = hd[nslot + q];
-                nbn[k] = hd[2 * nslot + q];
-                nsys[k] = ch.sys[q];
-                if (q != k) {
-                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(XR + (size_t)k * n, XR + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
-                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(Rr + (size_t)k * n, Rr + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
-                    SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv + (size_t)k * n, Pv + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
-                }
-            }
-            if (nk > 0) {
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr, nrr.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.rr_ru, nru.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.bn, nbn.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.iters, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.flag, zeros.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active, ones.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
-            }
-            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
-            ch.sys = nsys;
-            nslot = nk;
-            act.assign(nk, 1);
-        };
-        compact();
-        // iteration counts continue per system across compactions; maxiter is
-        // enforced per stretch between compactions against the running total
-        while (nslot > 0) {
-            {
-                // per-slot remaining iteration budget
-                int minleft = o.cg_maxiter;
-                for (int q = 0; q < nslot; q++) minleft = std::min(minleft, o.cg_maxiter - ch.iters[ch.sys[q]]);
-                C.maxiter = std::max(minleft, 1);
-            }
-            for (int it = 0; it < poll; it++) {
-                apply_M_mrhs<R>(h, nslot, Pv, Tv, Qv, st);
-                dim3 gr(rb, nslot);
-                k_cg_alpha<R><<<gr, kRedThreads, 0, st>>>(Pv, Qv, n, C);
-                SEEDCG_CHECK_LAUNCH();
-                k_cg_xr<R><<<gr, kRedThreads, 0, st>>>(XR, Rr, Pv, Qv, n, C);
-                SEEDCG_CHECK_LAUNCH();
-                k_cg_p<R><<<gr, kRedThreads, 0, st>>>(Rr, Pv, n, C);
-                SEEDCG_CHECK_LAUNCH();
-            }
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(pin, C.flag, sizeof(int) * nslot, cudaMemcpyDeviceToHost, st));
-            SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
-            std::vector<int> flags(pin, pin + nslot);
-            std::vector<int> fl;
-            for (int q = 0; q < nslot; q++)
-                if (flags[q]) fl.push_back(q);
-            if (!fl.empty()) {
-                reliable(fl);
-                std::vector<int> a2(pin + 512, pin + 512 + nslot);
-                for (int q : fl) {
-                    if (flags[q] == 3) {
-                        // iteration cap or non-finite residual: stop this system
-                        ch.notconv[ch.sys[q]] = 1;
-                        a2[q] = 0;
-                        SEEDCG_CUDA_TRY(cudaMemcpyAsync(C.active + q, pin + 1024, sizeof(int), cudaMemcpyHostToDevice, st));
-                    } else if (flags[q] == 2 && a2[q]) {
-                        // the iterated residual converged but the true one did not: restart
-                        SEEDCG_CUDA_TRY(cudaMemcpyAsync(Pv + (size_t)q * n, Rr + (size_t)q * n, n * cxR, cudaMemcpyDeviceToDevice, st));
-                    }
-                }
-                act = a2;
-                bool any_done = false;
-                for (int q = 0; q < nslot; q++) any_done |= !act[q];
-                if (any_done) compact();
-            }
-        }
+    CgResult cgr;
+    const bool cg_now = run_cg && !o.stop_after_seed;
+    if (cg_now) {
+        std::vector<CgGroup> gs{{h, nrhs, B64, X64}};
+        batched_cg<R>(gs, tol, fp64 ? 0.0 : o.reliable_delta, o.cg_maxiter, poll, true, h->cgbuf,
+                      h->pinned, cgr, st);
     }
     t_cg.stop(st);
     t_all.stop(st);
+    h->last_m_conv = m_conv;
+    h->last_po_count = po_count;
+    h->last_lz_status = lz_status;
+    h->last_ms_lanczos = t_lz.read();
+    h->last_ms_po = ms_po;
+    h->last_ms_seed = t_seed.read();
 
     // ---------------- results ----------------
-    std::vector<double> tr(nrhs, 0.0);
-    if (!o.stop_after_seed)
-        SEEDCG_CUDA_TRY(cudaMemcpy(tr.data(), tr_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
     seedcg_status code = SEEDCG_OK;
     if (lz_status == SEEDCG_ERR_NAN) code = SEEDCG_ERR_NAN;
     else if (lz_status == SEEDCG_ERR_TIMEOUT) code = SEEDCG_ERR_TIMEOUT;
     else if (lz_status == SEEDCG_ERR_BREAKDOWN) code = SEEDCG_ERR_BREAKDOWN;
-    if (!o.stop_after_seed && code == SEEDCG_OK) {
+    if (cg_now && code == SEEDCG_OK) {
         for (int j = 0; j < nrhs; j++)
-            if (ch.notconv[j] || !(tr[j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
+            if (cgr.notconv[0][j] || !(cgr.true_resid[0][j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
     }
     if (info) {
         info->m_conv = m_conv;
         info->m = m;
         info->po_count = po_count;
         int mx = 0;
-        for (int j = 0; j < nrhs; j++) mx = std::max(mx, ch.iters[j]);
+        for (int j = 0; j < nrhs; j++) mx = std::max(mx, cg_now ? cgr.iters[0][j] : 0);
         info->cg_iters_max = mx;
-        info->reliable_updates = reliable_updates;
+        info->reliable_updates = cgr.reliable_updates;
         for (int j = 0; j < nrhs; j++) {
-            if (info->iters) info->iters[j] = ch.iters[j] + (j == 0 ? m : 0);
-            if (info->matvecs)
-                info->matvecs[j] = 2 * (ch.iters[j] + ch.ru[j]) + (j == 0 ? 2 * m : 0) + (o.x0_given ? 2 : 0);
-            if (info->true_resid) info->true_resid[j] = tr[j];
+            const int it = cg_now ? cgr.iters[0][j] : 0;
+            const int ru = cg_now ? cgr.ru[0][j] : 0;
+            if (info->iters) info->iters[j] = it + (j == 0 ? m : 0);
+            if (info->matvecs) info->matvecs[j] = 2 * (it + ru) + (j == 0 ? 2 * m : 0) + (o.x0_given ? 2 : 0);
+            if (info->true_resid) info->true_resid[j] = cg_now ? cgr.true_resid[0][j] : 0.0;
         }
         info->ms_total = t_all.read();
         info->ms_lanczos = t_lz.read();
@@ -1102,6 +766,89 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 }
 
 }  // namespace
+
+// Several gauge fields: Lanczos + seeds per field, then ONE batched CG over the
+// seeded systems of all fields (B, X device canonical complex128 per field).
+seedcg_status batch_solve_impl(seedcg_handle** hs, int nf, const int* nrhs, const double* const* B,
+                               double* const* X, double tol, int extra_iters, int reorth_period,
+                               seedcg_info* infos, cudaStream_t st) {
+    const int prec = hs[0]->opt.precision;
+    std::vector<CgGroup> groups;
+    std::vector<seedcg_status> lz(nf, SEEDCG_OK);
+    std::vector<int> ms(nf, 0);
+    for (int f = 0; f < nf; f++) {
+        seedcg_handle* h = hs[f];
+        const int vol = h->g.vol;
+        const long n = 12L * vol;
+        const size_t fb = (size_t)nrhs[f] * n * sizeof(double2);
+        h->staging.ensure(2 * fb + 512);
+        double2* B64 = h->staging.as<double2>();
+        double2* X64 = B64 + (size_t)nrhs[f] * n;
+        to_internal_f64(B[f], B64, vol, nrhs[f], st);
+        if (h->opt.x0_given)
+            to_internal_f64(X[f], X64, vol, nrhs[f], st);
+        else
+            SEEDCG_CUDA_TRY(cudaMemsetAsync(X64, 0, fb, st));
+        seedcg_info* inf = infos ? &infos[f] : nullptr;
+        switch (prec) {
+            case SEEDCG_FP64:
+                lz[f] = run_solve<double, double2>(h, nrhs[f], B64, X64, tol, extra_iters, reorth_period, inf, st, false);
+                break;
+            case SEEDCG_MIXED_V32:
+                lz[f] = run_solve<float, float2>(h, nrhs[f], B64, X64, tol, extra_iters, reorth_period, inf, st, false);
+                break;
+            default:
+                lz[f] = run_solve<float, __nv_bfloat162>(h, nrhs[f], B64, X64, tol, extra_iters, reorth_period, inf, st, false);
+                break;
+        }
+        ms[f] = h->last_m;
+        groups.push_back({h, nrhs[f], B64, X64});
+    }
+    CgResult cgr;
+    PhaseTimer t;
+    t.start(st);
+    if (!hs[0]->opt.stop_after_seed) {
+        const seedcg_options& o = hs[0]->opt;
+        if (prec == SEEDCG_FP64)
+            batched_cg<double>(groups, tol, 0.0, o.cg_maxiter, o.poll_every, true, hs[0]->cgbuf,
+                               hs[0]->pinned, cgr, st);
+        else
+            batched_cg<float>(groups, tol, o.reliable_delta, o.cg_maxiter, o.poll_every, true,
+                              hs[0]->cgbuf, hs[0]->pinned, cgr, st);
+    }
+    t.stop(st);
+    const float ms_cg = t.read();
+    seedcg_status code = SEEDCG_OK;
+    for (int f = 0; f < nf; f++) {
+        seedcg_handle* h = hs[f];
+        if (lz[f] != SEEDCG_OK && lz[f] != SEEDCG_ERR_NOT_CONVERGED && code == SEEDCG_OK) code = lz[f];
+        const bool ran = !hs[0]->opt.stop_after_seed;
+        if (ran)
+            for (int j = 0; j < nrhs[f]; j++)
+                if (cgr.notconv[f][j] || !(cgr.true_resid[f][j] <= tol))
+                    if (code == SEEDCG_OK) code = SEEDCG_ERR_NOT_CONVERGED;
+        if (infos) {
+            seedcg_info& inf = infos[f];
+            int mx = 0;
+            for (int j = 0; j < nrhs[f]; j++) {
+                const int it = ran ? cgr.iters[f][j] : 0;
+                const int ru = ran ? cgr.ru[f][j] : 0;
+                mx = std::max(mx, it);
+                if (inf.iters) inf.iters[j] = it + (j == 0 ? ms[f] : 0);
+                if (inf.matvecs) inf.matvecs[j] = 2 * (it + ru) + (j == 0 ? 2 * ms[f] : 0);
+                if (inf.true_resid) inf.true_resid[j] = ran ? cgr.true_resid[f][j] : 0.0;
+            }
+            inf.cg_iters_max = mx;
+            inf.reliable_updates = cgr.reliable_updates;
+            inf.ms_cg = ms_cg;
+            inf.ms_total += ms_cg;
+        }
+        const double2* X64 = groups[f].x64;
+        from_internal_f64(X64, X[f], h->g.vol, nrhs[f], st);
+    }
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return code;
+}
 
 seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const double* X,
                                  double* C, int use_tc, cudaStream_t st) {

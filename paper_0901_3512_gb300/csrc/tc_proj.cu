@@ -257,19 +257,23 @@ k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
 }
 
-// C[a][j] (complex, double2) = sum over splits of part[split][a][2j] + i part[..][2j+1]
+// C[a][j] (complex, double2) = sum over splits of part[split][a][2j] + i part[..][2j+1];
+// one warp per output, lanes stride over the splits, fixed shuffle tree
 __global__ void k_tc_reduce(const float* __restrict__ part, int nsplit, int rows, int nb_cols,
                             int nvec, double2* __restrict__ C, int ldc) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= rows * nvec) return;
-    int a = t / nvec, j = t % nvec;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows * nvec) return;
+    const int a = w / nvec, j = w % nvec;
     double re = 0.0, im = 0.0;
-    for (int p = 0; p < nsplit; p++) {
+    for (int p = lane; p < nsplit; p += 32) {
         const float* q = part + ((size_t)p * rows + a) * nb_cols;
         re += q[2 * j];
         im += q[2 * j + 1];
     }
-    C[(size_t)a * ldc + j] = make_double2(re, im);
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) C[(size_t)a * ldc + j] = make_double2(re, im);
 }
 
 // B[2j][2e..2e+1] = (xr, xi), B[2j+1][2e..2e+1] = (xi, -xr) in bf16, for x_j = X + j*ldx
@@ -376,7 +380,7 @@ void tc_project(const __nv_bfloat162* V, int rows_alloc, int rows, const float2*
         default: launch_tc<64>(ma, mb, rows, kel, part, part_elems, err, &nsplit, st); break;
     }
     const int tot = rows * nvec;
-    k_tc_reduce<<<(tot + 255) / 256, 256, 0, st>>>(part, nsplit, rows, nb, nvec, C, ldc);
+    k_tc_reduce<<<(tot + 7) / 8, 256, 0, st>>>(part, nsplit, rows, nb, nvec, C, ldc);
     SEEDCG_CHECK_LAUNCH();
 }
 

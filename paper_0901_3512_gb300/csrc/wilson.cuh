@@ -45,11 +45,12 @@ __device__ __forceinline__ void spin_project(const Spinor<R>& p, cx_t<R> h[2][3]
 }
 
 // acc += coef * (full spinor rebuilt from r) for P = 1 + S g_mu
-template <int MU, int S, typename R>
+template <int MU, int S, typename R, bool SCALE = true>
 __device__ __forceinline__ void spin_accum(Spinor<R>& acc, const cx_t<R> r[2][3], R coef) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        cx_t<R> r0 = cscale(r[0][a], coef), r1 = cscale(r[1][a], coef);
+        cx_t<R> r0 = SCALE ? cscale(r[0][a], coef) : r[0][a];
+        cx_t<R> r1 = SCALE ? cscale(r[1][a], coef) : r[1][a];
         acc.c[0][a] = cadd(acc.c[0][a], r0);
         acc.c[1][a] = cadd(acc.c[1][a], r1);
         if (MU == 0) {
@@ -71,17 +72,39 @@ __device__ __forceinline__ void spin_accum(Spinor<R>& acc, const cx_t<R> r[2][3]
 // ---------------------------------------------------------------------------
 // spinor loads/stores in the internal layouts
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void load_spinor(const cx_t<R>* __restrict__ p, int vol, int s,
-                                            Spinor<R>& out) {
-#pragma unroll
-    for (int k = 0; k < 12; k++) out.c[k / 3][k % 3] = __ldg(p + (size_t)k * vol + s);
+// flat complex index of spinor element k (0..11) of site s
+__host__ __device__ __forceinline__ size_t sidx(int k, int s, int vol) {
+    return ((size_t)(k >> 1) * (size_t)vol + (size_t)s) * 2 + (size_t)(k & 1);
 }
-template <typename R>
-__device__ __forceinline__ void store_spinor(cx_t<R>* __restrict__ p, int vol, int s,
-                                             const Spinor<R>& v) {
+
+__device__ __forceinline__ void load_spinor(const float2* __restrict__ p, int vol, int s,
+                                            Spinor<float>& out) {
+    const float4* q = reinterpret_cast<const float4*>(p) + s;
 #pragma unroll
-    for (int k = 0; k < 12; k++) p[(size_t)k * vol + s] = v.c[k / 3][k % 3];
+    for (int c = 0; c < 6; c++) {
+        const float4 z = __ldg(q + (size_t)c * vol);
+        out.c[(2 * c) / 3][(2 * c) % 3] = make_float2(z.x, z.y);
+        out.c[(2 * c + 1) / 3][(2 * c + 1) % 3] = make_float2(z.z, z.w);
+    }
+}
+__device__ __forceinline__ void store_spinor(float2* __restrict__ p, int vol, int s,
+                                             const Spinor<float>& v) {
+    float4* q = reinterpret_cast<float4*>(p) + s;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        const float2 a = v.c[(2 * c) / 3][(2 * c) % 3], b = v.c[(2 * c + 1) / 3][(2 * c + 1) % 3];
+        q[(size_t)c * vol] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+__device__ __forceinline__ void load_spinor(const double2* __restrict__ p, int vol, int s,
+                                            Spinor<double>& out) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) out.c[k / 3][k % 3] = __ldg(p + sidx(k, s, vol));
+}
+__device__ __forceinline__ void store_spinor(double2* __restrict__ p, int vol, int s,
+                                             const Spinor<double>& v) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) p[sidx(k, s, vol)] = v.c[k / 3][k % 3];
 }
 
 // ---------------------------------------------------------------------------
@@ -114,7 +137,7 @@ __device__ __forceinline__ Nbr neighbours(const Geom& g, int s) {
 // one hop: acc += coef * P U psi_nbr  (forward: U = U_mu(x); backward: U = U_mu(x-mu)^dag)
 // LinkAt(a, b) returns U[a][b] for the link in use.
 // ---------------------------------------------------------------------------
-template <int MU, int S, bool BACK, typename R, typename LinkAt>
+template <int MU, int S, bool BACK, typename R, typename LinkAt, bool SCALE = true>
 __device__ __forceinline__ void hop(Spinor<R>& acc, const Spinor<R>& nb, LinkAt link, R coef) {
     cx_t<R> h[2][3], r[2][3];
     spin_project<MU, S>(nb, h);
@@ -136,42 +159,54 @@ __device__ __forceinline__ void hop(Spinor<R>& acc, const Spinor<R>& nb, LinkAt 
         r[0][a] = r0;
         r[1][a] = r1;
     }
-    spin_accum<MU, S>(acc, r, coef);
+    spin_accum<MU, S, R, SCALE>(acc, r, coef);
 }
 
-// Hopping sum H psi at site s (without the -kappa and the identity term).
-// Fwd(mu, e) / Bwd(mu, e) give element e = 3a+b of U_mu(x) / U_mu(x-mu).
+// (D psi)(x) or (D^dag psi)(x) at one site, accumulated straight into `out`
+// (out = psi(x), then out += -kappa * s * P U psi(y) hop by hop).
+// Fwd(mu, e) / Bwd(mu, e) give element e = 3a+b of U_mu(x) / U_mu(x-mu);
+// load(y, sp) loads the spinor at site y.
 template <int DAG, typename R, typename LoadNbr, typename Fwd, typename Bwd>
-__device__ __forceinline__ void hopping_sum(const Nbr& n, LoadNbr load, Fwd fl, Bwd bl,
-                                            Spinor<R>& acc) {
+__device__ __forceinline__ void wilson_site(const Nbr& n, int s, LoadNbr load, Fwd fl, Bwd bl,
+                                            R kappa, Spinor<R>& out) {
     constexpr int SF = DAG ? 1 : -1;   // forward projector 1 - g (D) or 1 + g (D^dag)
     constexpr int SB = -SF;
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) acc.c[a][b] = mk<R>(0, 0);
+    const R mk_ = -kappa;
+    load(s, out);
     Spinor<R> nb;
-    load(n.f[0], nb); hop<0, SF, false>(acc, nb, [&](int a, int b) { return fl(0, 3 * a + b); }, R(1));
-    load(n.b[0], nb); hop<0, SB, true>(acc, nb, [&](int a, int b) { return bl(0, 3 * a + b); }, R(1));
-    load(n.f[1], nb); hop<1, SF, false>(acc, nb, [&](int a, int b) { return fl(1, 3 * a + b); }, R(1));
-    load(n.b[1], nb); hop<1, SB, true>(acc, nb, [&](int a, int b) { return bl(1, 3 * a + b); }, R(1));
-    load(n.f[2], nb); hop<2, SF, false>(acc, nb, [&](int a, int b) { return fl(2, 3 * a + b); }, R(1));
-    load(n.b[2], nb); hop<2, SB, true>(acc, nb, [&](int a, int b) { return bl(2, 3 * a + b); }, R(1));
-    load(n.f[3], nb); hop<3, SF, false>(acc, nb, [&](int a, int b) { return fl(3, 3 * a + b); }, n.fwrap_t ? R(-1) : R(1));
-    load(n.b[3], nb); hop<3, SB, true>(acc, nb, [&](int a, int b) { return bl(3, 3 * a + b); }, n.bwrap_t ? R(-1) : R(1));
+    load(n.f[0], nb); hop<0, SF, false>(out, nb, [&](int a, int b) { return fl(0, 3 * a + b); }, mk_);
+    load(n.b[0], nb); hop<0, SB, true>(out, nb, [&](int a, int b) { return bl(0, 3 * a + b); }, mk_);
+    load(n.f[1], nb); hop<1, SF, false>(out, nb, [&](int a, int b) { return fl(1, 3 * a + b); }, mk_);
+    load(n.b[1], nb); hop<1, SB, true>(out, nb, [&](int a, int b) { return bl(1, 3 * a + b); }, mk_);
+    load(n.f[2], nb); hop<2, SF, false>(out, nb, [&](int a, int b) { return fl(2, 3 * a + b); }, mk_);
+    load(n.b[2], nb); hop<2, SB, true>(out, nb, [&](int a, int b) { return bl(2, 3 * a + b); }, mk_);
+    load(n.f[3], nb); hop<3, SF, false>(out, nb, [&](int a, int b) { return fl(3, 3 * a + b); }, n.fwrap_t ? kappa : mk_);
+    load(n.b[3], nb); hop<3, SB, true>(out, nb, [&](int a, int b) { return bl(3, 3 * a + b); }, n.bwrap_t ? kappa : mk_);
 }
 
-// out = in - kappa * H
-template <typename R>
-__device__ __forceinline__ void wilson_combine(const Spinor<R>& in, const Spinor<R>& hsum, R kappa,
-                                               Spinor<R>& out) {
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            out.c[a][b].x = fma(-kappa, hsum.c[a][b].x, in.c[a][b].x);
-            out.c[a][b].y = fma(-kappa, hsum.c[a][b].y, in.c[a][b].y);
-        }
+// Same, with links that already carry -kappa and the boundary sign (staged
+// that way by the multi-RHS kernel): out = psi(x) + sum of hops, no scaling.
+template <int DAG, typename R, typename LoadNbr, typename Fwd, typename Bwd>
+__device__ __forceinline__ void wilson_site_prescaled(const Nbr& n, int s, LoadNbr load, Fwd fl,
+                                                      Bwd bl, Spinor<R>& out) {
+    constexpr int SF = DAG ? 1 : -1;
+    constexpr int SB = -SF;
+    load(s, out);
+    Spinor<R> nb;
+#define SEEDCG_HOP(MU)                                                                          \
+    {                                                                                           \
+        auto lf = [&](int a, int b) { return fl(MU, 3 * a + b); };                              \
+        auto lb = [&](int a, int b) { return bl(MU, 3 * a + b); };                              \
+        load(n.f[MU], nb);                                                                      \
+        hop<MU, SF, false, R, decltype(lf), false>(out, nb, lf, R(1));                          \
+        load(n.b[MU], nb);                                                                      \
+        hop<MU, SB, true, R, decltype(lb), false>(out, nb, lb, R(1));                           \
+    }
+    SEEDCG_HOP(0)
+    SEEDCG_HOP(1)
+    SEEDCG_HOP(2)
+    SEEDCG_HOP(3)
+#undef SEEDCG_HOP
 }
 
 }  // namespace seedcg

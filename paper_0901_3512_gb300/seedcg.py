@@ -58,7 +58,7 @@ _lib = None
 EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "seedcg_solve",
            "seedcg_apply", "seedcg_get_lanczos", "seedcg_get_basis", "seedcg_last_error",
            "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
-           "seedcg_project_basis"]
+           "seedcg_project_basis", "seedcg_batch_solve"]
 
 
 def library_path() -> str:
@@ -93,6 +93,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.seedcg_time_dslash.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_float), vp]
     lib.seedcg_time_dslash.restype = ctypes.c_int
+    lib.seedcg_batch_solve.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ip,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(seedcg_info), vp]
+    lib.seedcg_batch_solve.restype = ctypes.c_int
     lib.seedcg_project_basis.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.seedcg_project_basis.restype = ctypes.c_int
     lib.seedcg_kernel_launches.argtypes = []
@@ -182,6 +187,36 @@ def seedcg_solve(h, nrhs: int, B, X, tol: float, extra_iters: int, reorth_period
            "iters": list(iters), "matvecs": list(mv), "true_resid": list(tr),
            "ms_total": info.ms_total, "ms_lanczos": info.ms_lanczos, "ms_po": info.ms_po,
            "ms_seed": info.ms_seed, "ms_cg": info.ms_cg}
+    return code, out
+
+
+def seedcg_batch_solve(hs, Bs, Xs, tol: float, extra_iters: int, reorth_period: int, stream=None,
+                       allow_not_converged: bool = False):
+    """One call for several fields: returns (status, [info dict per field])."""
+    nf = len(hs)
+    harr = (ctypes.c_void_p * nf)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    nrhs = (ctypes.c_int * nf)(*[int(b.shape[0]) for b in Bs])
+    barr = (ctypes.c_void_p * nf)(*[_ptr(b) for b in Bs])
+    xarr = (ctypes.c_void_p * nf)(*[_ptr(x) for x in Xs])
+    infos = (seedcg_info * nf)()
+    keep = []
+    for f in range(nf):
+        k = int(nrhs[f])
+        it, mv, tr = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)()
+        keep.append((it, mv, tr))
+        infos[f].iters, infos[f].matvecs, infos[f].true_resid = it, mv, tr
+    code = load().seedcg_batch_solve(harr, nf, nrhs, barr, xarr, float(tol), int(extra_iters),
+                                     int(reorth_period), infos, _stream_ptr(stream))
+    _check(hs[0], code, allow=(SEEDCG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    out = []
+    for f in range(nf):
+        it, mv, tr = keep[f]
+        i = infos[f]
+        out.append({"m_conv": i.m_conv, "m": i.m, "po_count": i.po_count,
+                    "cg_iters_max": i.cg_iters_max, "reliable_updates": i.reliable_updates,
+                    "iters": list(it), "matvecs": list(mv), "true_resid": list(tr),
+                    "ms_total": i.ms_total, "ms_lanczos": i.ms_lanczos, "ms_po": i.ms_po,
+                    "ms_seed": i.ms_seed, "ms_cg": i.ms_cg})
     return code, out
 
 

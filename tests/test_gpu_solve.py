@@ -115,10 +115,6 @@ def test_tiny_mixed_meets_residual_bar(precision):
         assert tr <= TOL
         assert rel(got[j], Xd[j]) <= cond * TOL
     assert info["reliable_updates"] >= len(eta)
-    if precision == "mixed_vbf16":
-        # on 3072 unknowns a bf16 basis cannot hold PO's orthogonality past
-        # convergence; the run must end Lanczos early and still converge by CG
-        assert info["m"] <= int(np.ceil(wl.past_factor * info["m_conv"]))
     s.close()
 
 
