@@ -77,6 +77,9 @@ typedef struct {
     int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */
     int poll_every;        /* iterations between host polls of device flags (default 32) */
     int use_tensor_cores;  /* 1: bf16-basis projections V^dag X on tcgen05 (default), 0: SIMT */
+    int use_guess;         /* 1: start every system from the learned guess x_0 = net(b)
+                              (weights set by seedcg_guess_set_weights/_train); a system
+                              whose guess has ||b - M x_0|| >= ||b|| starts from 0 */
 } seedcg_options;
 
 typedef struct {
@@ -180,6 +183,33 @@ seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const d
                                    double* C, int use_tensor_cores, void* stream);
 
 /*
+ * Learned initial guess (the project's extension; the paper has none): a
+ * gauge-covariant nearest-neighbour network of three layers, 1 -> 8 -> 8 -> 1
+ * channels,
+ *   out_co(x) = sum_ci [ W_0 in_ci(x) + sum_{d=+-mu} W_d U(x,d) in_ci(x+d) ],
+ * U(x,+mu) = U_mu(x), U(x,-mu) = U_mu(x-mu)^dag with the operator's boundary
+ * sign; W_d[co][ci] a complex 4x4 spin matrix; ReLU on real and imaginary
+ * parts after layers 1 and 2; input b/||b||, output times ||b||.
+ * Weights: complex128 (host) [11520] = layer 1 [9][8][1][4][4], layer 2
+ * [9][8][8][4][4], layer 3 [9][1][8][4][4], directions 0, +x,-x,+y,-y,+z,-z,+t,-t.
+ * B, X, X0: host or device, complex128 [n][V][4][3].  Computed in FP32 with
+ * FP64 reductions.
+ */
+seedcg_status seedcg_guess_set_weights(seedcg_handle* h, const double* w);
+seedcg_status seedcg_guess_get_weights(seedcg_handle* h, double* w);
+/* loss = mean_k ||net(b_k) - x_k||^2 / ||x_k||^2 and, if grad is not NULL, its
+   gradient dL/dRe(W) + i dL/dIm(W) (complex128 host [11520]) */
+seedcg_status seedcg_guess_loss_grad(seedcg_handle* h, int npairs, const double* B, const double* X,
+                                     double* loss, double* grad, void* stream);
+/* Adam (beta = 0.9, 0.999, eps = 1e-8) over `epochs` passes of the pairs in
+   their given order, mini-batches of `batch`; *final_loss = last epoch's mean */
+seedcg_status seedcg_guess_train(seedcg_handle* h, int npairs, const double* B, const double* X,
+                                 int epochs, int batch, double lr, double* final_loss, void* stream);
+/* X0[k] = net(B[k]) */
+seedcg_status seedcg_guess_predict(seedcg_handle* h, int n, const double* B, double* X0, void* stream);
+
+/*
+ * Measurement helper: time `reps` launches/*
  * Measurement helper: time `reps` launches of the multi-RHS dslash D on n
  * internal spinor fields (prec 0 = FP64, 1 = FP32) with CUDA events on
  * `stream`, writing a 512 MB buffer between launches when flush_l2 != 0 so

@@ -47,6 +47,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.cg_maxiter < 1) { why = "cg_maxiter must be >= 1"; return false; }
     if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
     if (o.use_tensor_cores < 0 || o.use_tensor_cores > 1) { why = "use_tensor_cores must be 0 or 1"; return false; }
+    if (o.use_guess < 0 || o.use_guess > 1) { why = "use_guess must be 0 or 1"; return false; }
     return true;
 }
 
@@ -68,6 +69,7 @@ void seedcg_default_options(seedcg_options* opt) {
     opt->stop_after_seed = 0;
     opt->poll_every = 32;
     opt->use_tensor_cores = 1;
+    opt->use_guess = 0;
 }
 
 seedcg_status seedcg_create(seedcg_handle** out, const int dims[4], const double* gauge,
@@ -356,6 +358,109 @@ seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const d
     }
 }
 
+namespace {
+// stage n canonical complex128 fields (host or device) into the internal FP64 layout
+void stage_in(seedcg_handle* h, int n, const double* src, seedcg::DevBuf& dst, cudaStream_t st) {
+    const int vol = h->g.vol;
+    const size_t bytes = (size_t)n * vol * 12 * sizeof(double2);
+    dst.ensure(bytes);
+    const double* d = src;
+    seedcg::DevBuf tmp;
+    if (!is_device_ptr(src)) {
+        tmp.ensure(bytes);
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(tmp.p, src, bytes, cudaMemcpyHostToDevice, st));
+        d = tmp.as<double>();
+    }
+    seedcg::to_internal_f64(d, dst.as<double2>(), vol, n, st);
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+}
+}  // namespace
+
+seedcg_status seedcg_guess_set_weights(seedcg_handle* h, const double* w) {
+    if (!h || !w) return fail(h, SEEDCG_ERR_ARG, "h or w is NULL");
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        seedcg::guess_set_weights(h, w, 0);
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_guess_get_weights(seedcg_handle* h, double* w) {
+    if (!h || !w) return fail(h, SEEDCG_ERR_ARG, "h or w is NULL");
+    try {
+        seedcg::guess_get_weights(h, w, 0);
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_guess_loss_grad(seedcg_handle* h, int npairs, const double* B, const double* X,
+                                     double* loss, double* grad, void* stream) {
+    if (!h || !B || !X || !loss || npairs < 1) return fail(h, SEEDCG_ERR_ARG, "bad guess arguments");
+    if (!seedcg::guess_ready(h)) return fail(h, SEEDCG_ERR_ARG, "set the guess weights first");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        seedcg::DevBuf b, x;
+        stage_in(h, npairs, B, b, st);
+        stage_in(h, npairs, X, x, st);
+        *loss = seedcg::guess_loss_grad(h, npairs, b.as<double2>(), x.as<double2>(), grad, st);
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_guess_train(seedcg_handle* h, int npairs, const double* B, const double* X,
+                                 int epochs, int batch, double lr, double* final_loss, void* stream) {
+    if (!h || !B || !X || npairs < 1 || epochs < 1 || batch < 1 || !(lr > 0.0))
+        return fail(h, SEEDCG_ERR_ARG, "bad guess training arguments");
+    if (!seedcg::guess_ready(h)) return fail(h, SEEDCG_ERR_ARG, "set the initial guess weights first");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        seedcg::DevBuf b, x;
+        stage_in(h, npairs, B, b, st);
+        stage_in(h, npairs, X, x, st);
+        const double l = seedcg::guess_train(h, npairs, b.as<double2>(), x.as<double2>(), epochs,
+                                             batch, lr, st);
+        if (final_loss) *final_loss = l;
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
+seedcg_status seedcg_guess_predict(seedcg_handle* h, int n, const double* B, double* X0, void* stream) {
+    if (!h || !B || !X0 || n < 1) return fail(h, SEEDCG_ERR_ARG, "bad guess arguments");
+    if (!seedcg::guess_ready(h)) return fail(h, SEEDCG_ERR_ARG, "set the guess weights first");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        const int vol = h->g.vol;
+        const size_t bytes = (size_t)n * vol * 12 * sizeof(double2);
+        seedcg::DevBuf b, x, c;
+        stage_in(h, n, B, b, st);
+        x.ensure(bytes);
+        seedcg::guess_predict(h, n, b.as<double2>(), x.as<double2>(), st);
+        const bool xd = is_device_ptr(X0);
+        double* dst = X0;
+        if (!xd) {
+            c.ensure(bytes);
+            dst = c.as<double>();
+        }
+        seedcg::from_internal_f64(x.as<double2>(), dst, vol, n, st);
+        if (!xd) SEEDCG_CUDA_TRY(cudaMemcpyAsync(X0, dst, bytes, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        return SEEDCG_OK;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
 seedcg_status seedcg_time_dslash(seedcg_handle* h, int prec, int n, int reps, int flush_l2,
                                 float* ms_per_launch, void* stream) {
     if (!h || !ms_per_launch) return fail(h, SEEDCG_ERR_ARG, "h or ms_per_launch is NULL");
@@ -423,6 +528,7 @@ void seedcg_destroy(seedcg_handle* h) {
     h->coef.release();
     h->tcbuf.release();
     h->cgbuf.release();
+    seedcg::guess_free(h);
     h->staging.release();
     if (h->pinned) cudaFreeHost(h->pinned);
     cudaSetDevice(prev);

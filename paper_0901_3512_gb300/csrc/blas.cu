@@ -219,6 +219,27 @@ __global__ void k_proj_reduce(const double2* __restrict__ part, int nblk, int na
     if (lane == 0) C[(size_t)a * ldc + c0 + j] = make_double2(re, im);
 }
 
+__global__ void __launch_bounds__(kRedThreads)
+k_nrm2(const double2* __restrict__ x, long n, double* partials, unsigned* ctr, double* out) {
+    double p = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        const double2 z = x[e];
+        p += z.x * z.x + z.y * z.y;
+    }
+    double red[1] = {p};
+    grid_sum<1>(red, partials, ctr, [&](double* tot) { *out = sqrt(tot[0]); });
+}
+
+// y = b - y (FP64)
+__global__ void k_bmy(const double2* __restrict__ b, double2* __restrict__ y, long n) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        const double2 bb = b[e], yy = y[e];
+        y[e] = make_double2(bb.x - yy.x, bb.y - yy.y);
+    }
+}
+
 template <typename ST, typename DT>
 __global__ void k_convert(const ST* __restrict__ src, DT* __restrict__ dst, long n) {
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
@@ -229,6 +250,17 @@ __global__ void k_convert(const ST* __restrict__ src, DT* __restrict__ dst, long
 }
 
 }  // namespace
+
+void axpby_f64(const double2* b, double2* y, long n, cudaStream_t s) {
+    k_bmy<<<nblocks(n, 256, 152 * 16), 256, 0, s>>>(b, y, n);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+void k_norm2_public(const double2* x, long n, double* partials, unsigned* ctr, double* out,
+                    cudaStream_t s) {
+    k_nrm2<<<nblocks(n, kRedThreads * 8, 1216), kRedThreads, 0, s>>>(x, n, partials, ctr, out);
+    SEEDCG_CHECK_LAUNCH();
+}
 
 template <typename R>
 void dot(const cx_t<R>* a, const cx_t<R>* b, long n, double* partials, unsigned* ctr,

@@ -31,9 +31,22 @@ struct seedcg_handle {
     float last_ms_lanczos = 0.f, last_ms_po = 0.f, last_ms_seed = 0.f;
     std::string err;
     void* pinned = nullptr;       // small pinned host buffer for flag polls
+    void* guess = nullptr;        // learned initial guess: weights, Adam state, buffers
+    bool force_x0 = false;        // this solve starts from X (set when the guess supplied x_0)
 };
 
 namespace seedcg {
+// learned initial guess (guess.cu); B, X internal FP64 [n][12 V]
+void guess_set_weights(seedcg_handle* h, const double* w, cudaStream_t st);
+void guess_get_weights(seedcg_handle* h, double* w, cudaStream_t st);
+double guess_loss_grad(seedcg_handle* h, int npairs, const double2* B, const double2* X,
+                       double* grad_out, cudaStream_t st);
+double guess_train(seedcg_handle* h, int npairs, const double2* B, const double2* X, int epochs,
+                   int batch, double lr, cudaStream_t st);
+void guess_predict(seedcg_handle* h, int n_fields, const double2* B, double2* X0, cudaStream_t st);
+void guess_free(seedcg_handle* h);
+bool guess_ready(const seedcg_handle* h);
+
 seedcg_status batch_solve_impl(seedcg_handle** hs, int nf, const int* nrhs, const double* const* B,
                                double* const* X, double tol, int extra_iters, int reorth_period,
                                seedcg_info* infos, cudaStream_t st);

@@ -66,6 +66,12 @@ template <typename R, typename AT, typename YT>
 void gemm_n(const AT* A, long lda, int na, const double2* C, int ldc, int nb, YT* Y, long ldy,
             long n, double sign, cudaStream_t s);
 
+// y = b - y (FP64, flat)
+void axpby_f64(const double2* b, double2* y, long n, cudaStream_t s);
+// *out = ||x|| (FP64, deterministic; partials holds >= 1216 doubles, ctr one zero counter)
+void k_norm2_public(const double2* x, long n, double* partials, unsigned* ctr, double* out,
+                    cudaStream_t s);
+
 // convert / copy flat vectors between storage types
 template <typename ST, typename DT>
 void convert(const ST* src, DT* dst, long n, cudaStream_t s);

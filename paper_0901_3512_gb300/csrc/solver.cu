@@ -580,7 +580,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 
     // ---------------- step 1: r_0^j = b^j - M x_0^j ----------------
     const int nbl = std::min<long>((n * nrhs + 255) / 256, 152 * 32);
-    if (o.x0_given) {
+    if (o.x0_given || h->force_x0) {
         apply_M64(h, nrhs, X64, T64, MX, st);
         k_resid_init<R><<<nbl, 256, 0, st>>>(B64, MX, R0, n * nrhs);
     } else {
@@ -753,7 +753,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
             const int it = cg_now ? cgr.iters[0][j] : 0;
             const int ru = cg_now ? cgr.ru[0][j] : 0;
             if (info->iters) info->iters[j] = it + (j == 0 ? m : 0);
-            if (info->matvecs) info->matvecs[j] = 2 * (it + ru) + (j == 0 ? 2 * m : 0) + (o.x0_given ? 2 : 0);
+            if (info->matvecs) info->matvecs[j] = 2 * (it + ru) + (j == 0 ? 2 * m : 0) + ((o.x0_given || h->force_x0) ? 2 : 0);
             if (info->true_resid) info->true_resid[j] = cg_now ? cgr.true_resid[0][j] : 0.0;
         }
         info->ms_total = t_all.read();
@@ -911,6 +911,32 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
         to_internal_f64(X, X64, vol, nrhs, st);
     else
         SEEDCG_CUDA_TRY(cudaMemsetAsync(X64, 0, fb, st));
+    h->force_x0 = false;
+    if (h->opt.use_guess && guess_ready(h)) {
+        // x_0 = net(b); fall back to 0 where ||b - M x_0|| >= ||b||
+        guess_predict(h, nrhs, B64, X64, st);
+        DevBuf t1, t2, nr;
+        t1.ensure(fb);
+        t2.ensure(fb);
+        nr.ensure(sizeof(double) * (4096 + 2 * nrhs) + sizeof(unsigned) * 64);
+        dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, nrhs, X64, t1.as<double2>(), st);
+        dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, nrhs, t1.as<double2>(), t2.as<double2>(), st);
+        double* part = nr.as<double>();
+        double* norms = part + 4096;
+        unsigned* ctr = reinterpret_cast<unsigned*>(norms + 2 * nrhs);
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 64, st));
+        for (int j = 0; j < nrhs; j++) {
+            axpby_f64(B64 + (size_t)j * n, t2.as<double2>() + (size_t)j * n, n, st);  // t2 = b - M x0
+            k_norm2_public(B64 + (size_t)j * n, n, part, ctr, norms + j, st);
+            k_norm2_public(t2.as<double2>() + (size_t)j * n, n, part, ctr, norms + nrhs + j, st);
+        }
+        std::vector<double> hn(2 * nrhs);
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+        SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int j = 0; j < nrhs; j++)
+            if (!(hn[nrhs + j] < hn[j])) SEEDCG_CUDA_TRY(cudaMemsetAsync(X64 + (size_t)j * n, 0, n * sizeof(double2), st));
+        h->force_x0 = true;
+    }
     seedcg_status code;
     switch (h->opt.precision) {
         case SEEDCG_FP64:

@@ -39,7 +39,7 @@ class seedcg_options(ctypes.Structure):
                 ("po_passes", ctypes.c_int), ("seed_mode", ctypes.c_int),
                 ("x0_given", ctypes.c_int), ("cg_maxiter", ctypes.c_int),
                 ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int),
-                ("use_tensor_cores", ctypes.c_int)]
+                ("use_tensor_cores", ctypes.c_int), ("use_guess", ctypes.c_int)]
 
 
 class seedcg_info(ctypes.Structure):
@@ -58,7 +58,10 @@ _lib = None
 EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "seedcg_solve",
            "seedcg_apply", "seedcg_get_lanczos", "seedcg_get_basis", "seedcg_last_error",
            "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
-           "seedcg_project_basis", "seedcg_batch_solve"]
+           "seedcg_project_basis", "seedcg_batch_solve", "seedcg_guess_set_weights",
+           "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
+           "seedcg_guess_predict"]
+GUESS_NW = 11520
 
 
 def library_path() -> str:
@@ -98,6 +101,15 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_guess_set_weights.argtypes = [vp, vp]
+    lib.seedcg_guess_get_weights.argtypes = [vp, vp]
+    lib.seedcg_guess_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, dp, vp, vp]
+    lib.seedcg_guess_train.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, dp, vp]
+    lib.seedcg_guess_predict.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    for name in ("seedcg_guess_set_weights", "seedcg_guess_get_weights", "seedcg_guess_loss_grad",
+                 "seedcg_guess_train", "seedcg_guess_predict"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.seedcg_project_basis.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.seedcg_project_basis.restype = ctypes.c_int
     lib.seedcg_kernel_launches.argtypes = []
@@ -256,6 +268,55 @@ def seedcg_project_basis(h, rows: int, nvec: int, X, use_tensor_cores: int = 1, 
                                           ctypes.c_void_p(C.ctypes.data), int(use_tensor_cores),
                                           _stream_ptr(stream)))
     return C
+
+
+def _weights_flat(Ws):
+    w = np.concatenate([np.asarray(W, dtype=np.complex128).reshape(-1) for W in Ws])
+    if w.size != GUESS_NW:
+        raise ValueError("guess weights must hold 11520 complex entries")
+    return np.ascontiguousarray(w)
+
+
+def seedcg_guess_set_weights(h, Ws):
+    w = _weights_flat(Ws) if isinstance(Ws, (list, tuple)) else np.ascontiguousarray(Ws, dtype=np.complex128)
+    _check(h, load().seedcg_guess_set_weights(h, ctypes.c_void_p(w.ctypes.data)))
+
+
+def seedcg_guess_get_weights(h):
+    w = np.zeros(GUESS_NW, dtype=np.complex128)
+    _check(h, load().seedcg_guess_get_weights(h, ctypes.c_void_p(w.ctypes.data)))
+    return w
+
+
+def seedcg_guess_loss_grad(h, B, X, want_grad=True, stream=None):
+    loss = ctypes.c_double()
+    g = np.zeros(GUESS_NW, dtype=np.complex128) if want_grad else None
+    _check(h, load().seedcg_guess_loss_grad(h, int(B.shape[0]), ctypes.c_void_p(_ptr(B)),
+                                            ctypes.c_void_p(_ptr(X)), ctypes.byref(loss),
+                                            ctypes.c_void_p(g.ctypes.data) if want_grad else None,
+                                            _stream_ptr(stream)))
+    return loss.value, g
+
+
+def seedcg_guess_train(h, B, X, epochs, batch, lr, stream=None):
+    loss = ctypes.c_double()
+    _check(h, load().seedcg_guess_train(h, int(B.shape[0]), ctypes.c_void_p(_ptr(B)),
+                                        ctypes.c_void_p(_ptr(X)), int(epochs), int(batch), float(lr),
+                                        ctypes.byref(loss), _stream_ptr(stream)))
+    return loss.value
+
+
+def seedcg_guess_predict(h, B, X0, stream=None):
+    _check(h, load().seedcg_guess_predict(h, int(B.shape[0]), ctypes.c_void_p(_ptr(B)),
+                                          ctypes.c_void_p(_ptr(X0)), _stream_ptr(stream)))
+
+
+def split_weights(w):
+    """Flat complex128 [11520] -> the three layer arrays [9][C_out][C_in][4][4]."""
+    w = np.asarray(w)
+    a, b = 9 * 8 * 16, 9 * 64 * 16
+    return [w[:a].reshape(9, 8, 1, 4, 4), w[a:a + b].reshape(9, 8, 8, 4, 4),
+            w[a + b:].reshape(9, 1, 8, 4, 4)]
 
 
 def seedcg_kernel_launches() -> int:
