@@ -47,6 +47,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample-iters", type=int, default=24)
+    p.add_argument("--record-units", action="store_true",
+                   help="write this run's work units (m, CG iterations) for the reference arm")
+    p.add_argument("--compare-fp64", action="store_true",
+                   help="also time one plain FP64 solve of the same workload (slow)")
     return p.parse_args()
 
 
@@ -322,6 +326,31 @@ def run_ours(args):
                          f"{len(range(k, m + 1, k))} PO steps, {cg_total} CG iterations)",
                "per_unit_s": {kk: costs[kk] for kk in ("t_lanczos_iter", "t_po_row", "t_cg_iter")}}
 
+    fp64_cmp = None
+    if args.compare_fp64 and rank == 0:
+        s64 = seedcg.Solver(f.dims, gauge, kappa, precision="fp64", past_factor=wl.past_factor,
+                            m_max=args.m_max)
+        X64 = torch.zeros_like(B)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        c64, i64 = s64.solve(B, X64, wl.tol, 0, k, stream=stream, allow_not_converged=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        t64 = ea.elapsed_time(eb) / 1000.0
+        fp64_cmp = {"seconds": t64, "status": c64, "m_conv": i64["m_conv"], "m": i64["m"],
+                    "max_true_resid": max(i64["true_resid"]), "ms_po": i64["ms_po"],
+                    "ms_cg": i64["ms_cg"], "speedup_mixed_over_fp64": t64 / (ms_max / 1000.0)}
+        s64.close()
+
+    if args.record_units and rank == 0:
+        units_path = os.path.join(ROOT, "paper_0901_3512_gb300", "workload_units.json")
+        table = json.load(open(units_path)) if os.path.exists(units_path) else {}
+        table[args.workload] = {"m": m, "m_conv": info["m_conv"],
+                                "cg_iters_total": sum(info["iters"]) - m,
+                                "precision": prec, "recorded_by": "bench.py --record-units"}
+        with open(units_path, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+
     if rank == 0:
         out = {"metric": METRIC, "value": ms_max / 1000.0 / world, "unit": "s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -344,6 +373,8 @@ def run_ours(args):
                "roofline": roofline, "dslash": dslash, "clocks": clocks,
                "gpu_launches": launches // max(args.steps, 1) * args.steps,
                "e2e": e2e, "cpu_baseline": cpu}
+        if fp64_cmp:
+            out["fp64_plain"] = fp64_cmp
         print(json.dumps(out))
     s.close()
     if world > 1:

@@ -17,7 +17,10 @@
 // (x64 += x_R, r = b - M x64 in FP64) and compacts the active systems.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "cg_batch.cuh"
@@ -31,7 +34,8 @@ namespace {
 
 constexpr int kMaxGroups = 16;
 constexpr int TS = 32;       // sites per dslash tile (one warp per right-hand side)
-constexpr int RPB = 8;       // right-hand sides processed side by side per tile
+// right-hand sides processed side by side per tile (warps per block): picked
+// per batch by the autotuner below from {4, 8, 12}
 
 template <typename R>
 struct GroupDev {
@@ -80,8 +84,8 @@ __device__ __forceinline__ int find_group(int b, int ng, const int* tile0) {
 // ---------------------------------------------------------------------------
 // 1/2: multi-field multi-RHS dslash (DAG = 0: t = D p; DAG = 1: q = D^dag t [+ dot])
 // ---------------------------------------------------------------------------
-template <typename R, int DAG, bool DOT>
-__global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? 3 : 1))
+template <typename R, int DAG, bool DOT, int RPB>
+__global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? (RPB <= 8 ? 3 : 2) : 1))
 k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
     __shared__ cx_t<R> sl[2][4][9][TS];
     __shared__ int sb[4][TS];
@@ -341,6 +345,99 @@ k_norm_rows(const T* __restrict__ base, long n, double* partials, unsigned* coun
     rowsum<1>(red, partials, counters, [&](double* tot) { out[k] = sqrt(tot[0]); });
 }
 
+// ---------------------------------------------------------------------------
+// autotuner: the multi-field dslash's warps per tile (right-hand sides side by
+// side) is timed with CUDA events on the batch's own vectors for each candidate
+// and the fastest kept; results are cached in memory per batch signature and,
+// when SEEDCG_TUNE_CACHE names a file, in that file ("key rpb" lines).
+// ---------------------------------------------------------------------------
+template <typename R>
+void launch_mf(int rpb, int dag, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+#define SEEDCG_MF(RP)                                                                          \
+    if (dag) k_mf_dslash<R, 1, true, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows);           \
+    else k_mf_dslash<R, 0, false, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows);
+    if (rpb == 4) { SEEDCG_MF(4) }
+    else if (rpb == 12) { SEEDCG_MF(12) }
+    else { SEEDCG_MF(8) }
+#undef SEEDCG_MF
+    SEEDCG_CHECK_LAUNCH();
+}
+
+std::string tune_key(const std::vector<CgGroup>& groups, bool fp64) {
+    std::string k = fp64 ? "mf_dslash f64" : "mf_dslash f32";
+    for (auto& g : groups) {
+        char b[96];
+        snprintf(b, sizeof(b), " %dx%dx%dx%d:%d", g.h->g.L[0], g.h->g.L[1], g.h->g.L[2], g.h->g.L[3], g.nsys);
+        k += b;
+    }
+    cudaDeviceProp p;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) k += std::string(" ") + p.name;
+    for (auto& c : k) if (c == ' ') c = '_';
+    return k;
+}
+
+std::vector<std::pair<std::string, int>>& tune_table() {
+    static std::vector<std::pair<std::string, int>> t;
+    static bool loaded = false;
+    if (!loaded) {
+        loaded = true;
+        const char* path = getenv("SEEDCG_TUNE_CACHE");
+        if (path) {
+            FILE* f = fopen(path, "r");
+            if (f) {
+                char key[512];
+                int v;
+                while (fscanf(f, "%511s %d", key, &v) == 2) t.push_back({key, v});
+                fclose(f);
+            }
+        }
+    }
+    return t;
+}
+
+template <typename R>
+int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const GroupDev<R>* gdev, int ng,
+                 Rows rows, cudaStream_t st) {
+    const std::string key = tune_key(groups, sizeof(R) == 8);
+    for (auto& e : tune_table())
+        if (e.first == key) return e.second;
+    const int cands[3] = {4, 8, 12};
+    cudaEvent_t a, b;
+    SEEDCG_CUDA_TRY(cudaEventCreate(&a));
+    SEEDCG_CUDA_TRY(cudaEventCreate(&b));
+    int best = 8;
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        launch_mf<R>(c, 0, tiles, st, gdev, ng, rows);  // warm-up
+        SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
+        for (int r = 0; r < 3; r++) {
+            launch_mf<R>(c, 0, tiles, st, gdev, ng, rows);
+            launch_mf<R>(c, 1, tiles, st, gdev, ng, rows);
+        }
+        SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
+        SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        SEEDCG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    tune_table().push_back({key, best});
+    if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
+        FILE* f = fopen(path, "a");
+        if (f) {
+            fprintf(f, "%s %d\n", key.c_str(), best);
+            fclose(f);
+        }
+    }
+    return best;
+}
+
 struct Carve2 {
     char* base;
     size_t off = 0;
@@ -597,12 +694,12 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
 
     // ---- the iteration chunk (graph-captured) ----
     const int gx = rblocks;
+    const int rpb = nrows > 0 ? autotune_rpb<R>(groups, tiles, gdev, ng, rows, st) : 8;
+    out.rpb = rpb;
     auto chunk = [&](cudaStream_t s) {
         for (int it = 0; it < poll; it++) {
-            k_mf_dslash<R, 0, false><<<tiles, TS * RPB, 0, s>>>(gdev, ng, rows);
-            SEEDCG_CHECK_LAUNCH();
-            k_mf_dslash<R, 1, true><<<tiles, TS * RPB, 0, s>>>(gdev, ng, rows);
-            SEEDCG_CHECK_LAUNCH();
+            launch_mf<R>(rpb, 0, tiles, s, gdev, ng, rows);
+            launch_mf<R>(rpb, 1, tiles, s, gdev, ng, rows);
             k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
             dim3 gr(gx, rows_cap);

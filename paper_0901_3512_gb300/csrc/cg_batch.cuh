@@ -23,6 +23,7 @@ struct CgResult {
     std::vector<std::vector<double>> true_resid;
     int reliable_updates = 0;
     int graph_chunks = 0;
+    int rpb = 0;          // warps per dslash tile chosen by the autotuner
 };
 
 // Run CG on every system of every group until ||b - M x|| <= tol ||b|| in FP64.
