@@ -51,6 +51,9 @@ def _args():
                    help="write this run's work units (m, CG iterations) for the reference arm")
     p.add_argument("--compare-fp64", action="store_true",
                    help="also time one plain FP64 solve of the same workload (slow)")
+    p.add_argument("--only", default=None, choices=["dslash", "po"],
+                   help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
+                        "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
     return p.parse_args()
 
 
@@ -381,8 +384,36 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    """Small runs of single kernels for ncu captures (not bench lines)."""
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[args.workload]
+    f = wl.fields[0]
+    prec = args.precision or wl.precision
+    s = seedcg.Solver(f.dims, f.gauge(), W.kappa_for(f.name), precision=prec,
+                      past_factor=wl.past_factor, m_max=args.m_max)
+    if args.only == "dslash":
+        ms = s.time_dslash(prec=1, n=wl.nrhs[0], reps=max(args.steps, 1))
+        print(json.dumps({"only": "dslash", "ms": ms}))
+    else:
+        eta = torch.from_numpy(wl.sources_for(0)).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        X = torch.zeros_like(B)
+        s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max,
+                      stop_after_seed=1)
+        code, info = s.solve(B, X, wl.tol, 0, wl.reorth_period, allow_not_converged=True)
+        print(json.dumps({"only": "po", "m": info["m"], "ms_po": info["ms_po"],
+                          "po_count": info["po_count"]}))
+    s.close()
+
+
 def main():
     args = _args()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
