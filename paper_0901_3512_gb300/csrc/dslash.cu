@@ -1,6 +1,13 @@
 // Wilson dslash kernels (single- and multi-right-hand-side, FP64 and FP32)
 // and the layout transforms between the boundary's complex128 AoS and the
 // internal site-fastest layouts.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 #include "wilson.cuh"
 
@@ -274,11 +281,11 @@ int largest_divisor_at_most(int L, int cap) {
     return best;
 }
 
-bool make_brick(const Geom& g, Brick& br) {
+bool make_brick(const Geom& g, Brick& br, int cap = 128) {
     br.bx = g.L[0];
-    if (br.bx > 64) return false;
-    br.by = largest_divisor_at_most(g.L[1], 64 / br.bx);
-    br.bz = largest_divisor_at_most(g.L[2], 128 / (br.bx * br.by));
+    if (br.bx > 64 || br.bx > cap) return false;
+    br.by = largest_divisor_at_most(g.L[1], (cap / 2 > br.bx ? cap / 2 : cap) / br.bx);
+    br.bz = largest_divisor_at_most(g.L[2], cap / (br.bx * br.by));
     br.tb = br.bx * br.by * br.bz;
     br.ny = g.L[1] / br.by;
     br.nz = g.L[2] / br.bz;
@@ -312,17 +319,101 @@ void launch_dslash(const Geom& g, const cx_t<R>* u, R kappa, int dag, const cx_t
     SEEDCG_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// autotuner of the brick kernel: sites per brick (64 / 128) and right-hand
+// sides side by side per block, timed with CUDA events on the caller's own
+// buffers at the first call for a (lattice, n, precision, D or D^dag) and kept
+// for the process (and in SEEDCG_TUNE_CACHE when set).
+// ---------------------------------------------------------------------------
+struct BrickChoice {
+    int cap;
+    int rpb;   // 0 = balanced default
+};
+
 template <typename R>
 void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n,
                         const cx_t<R>* in, cx_t<R>* out, cudaStream_t st,
                         const cx_t<R>* pdot = nullptr, double* part = nullptr,
-                        int* nblocks_out = nullptr) {
+                        int* nblocks_out = nullptr, const BrickChoice* force = nullptr);
+
+template <typename R>
+BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n, const cx_t<R>* in,
+                        cx_t<R>* out, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<std::string, BrickChoice> cache;
+    char key[160];
+    snprintf(key, sizeof(key), "brick_%s_%dx%dx%dx%d_n%d_dag%d", sizeof(R) == 8 ? "f64" : "f32",
+             g.L[0], g.L[1], g.L[2], g.L[3], n, dag);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+        if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
+            FILE* f = fopen(path, "r");
+            if (f) {
+                char k[512];
+                int a, b;
+                while (fscanf(f, "%511s %d %d", k, &a, &b) == 3)
+                    if (std::string(k) == key) cache[key] = BrickChoice{a, b};
+                fclose(f);
+                it = cache.find(key);
+                if (it != cache.end()) return it->second;
+            }
+        }
+    }
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap_status);
+    if (cap_status != cudaStreamCaptureStatusNone) return BrickChoice{128, 0};  // no timing inside a capture
+    const BrickChoice cands[] = {{128, 0}, {128, 2}, {128, 1}, {64, 0}, {64, 4}, {64, 3}};
+    cudaEvent_t a, b;
+    SEEDCG_CUDA_TRY(cudaEventCreate(&a));
+    SEEDCG_CUDA_TRY(cudaEventCreate(&b));
+    BrickChoice best{128, 0};
+    float best_ms = 1e30f;
+    for (const BrickChoice& c : cands) {
+        Brick br;
+        if (!make_brick(g, br, c.cap) || !(br.tb == 64 || br.tb == 96 || br.tb == 128)) continue;
+        launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, nullptr, nullptr, nullptr, &c);
+        SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
+        for (int r = 0; r < 3; r++)
+            launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, nullptr, nullptr, nullptr, &c);
+        SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
+        SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        SEEDCG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
+        FILE* f = fopen(path, "a");
+        if (f) {
+            fprintf(f, "%s %d %d\n", key, best.cap, best.rpb);
+            fclose(f);
+        }
+    }
+    return best;
+}
+
+template <typename R>
+void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n,
+                        const cx_t<R>* in, cx_t<R>* out, cudaStream_t st,
+                        const cx_t<R>* pdot, double* part, int* nblocks_out,
+                        const BrickChoice* force) {
     if (n <= 0) return;
     Brick br;
-    if (make_brick(g, br) && (br.tb == 64 || br.tb == 96 || br.tb == 128)) {
+    BrickChoice ch{128, 0};
+    if (force) ch = *force;
+    else if (!pdot) ch = tuned_brick<R>(g, u, kappa, dag, n, in, out, st);
+    if (make_brick(g, br, ch.cap) && (br.tb == 64 || br.tb == 96 || br.tb == 128)) {
         const int maxr = 384 / br.tb;
         const int passes = (n + maxr - 1) / maxr;
-        const int rpb = (n + passes - 1) / passes;
+        const int rpb = ch.rpb > 0 ? std::min(ch.rpb, maxr) : (n + passes - 1) / passes;
         const int threads = br.tb * rpb;
         const size_t smem = (size_t)br.tb * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
         const int nb = br.ny * br.nz * g.L[3];
