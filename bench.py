@@ -211,6 +211,58 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """Several uneven gauge fields in one seedcg_batch_solve (one step = one call)."""
+    import torch
+
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    wl = W.WORKLOADS[args.workload]
+    prec = args.precision or wl.precision
+    solvers, Bs, Xs = [], [], []
+    for i, f in enumerate(wl.fields):
+        s = seedcg.Solver(f.dims, f.gauge(), W.kappa_for(f.name), precision=prec,
+                          past_factor=wl.past_factor, m_max=args.m_max)
+        eta = torch.from_numpy(wl.sources_for(i)).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        solvers.append(s)
+        Bs.append(B)
+        Xs.append(torch.zeros_like(B))
+    hs = [s.h for s in solvers]
+    for _ in range(args.warmup):
+        seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = seedcg.seedcg_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        code, infos = seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = {"metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": prec, "data": "synthetic",
+           "config": {"workload": args.workload,
+                      "fields": [{"lattice": list(f.dims), "nrhs": n, "kappa": W.kappa_for(f.name)}
+                                 for f, n in zip(wl.fields, wl.nrhs)],
+                      "sources": wl.sources, "tol": wl.tol, "reorth_period": wl.reorth_period},
+           "valid": code == 0 and all(max(i["true_resid"]) <= wl.tol for i in infos),
+           "fields": [{"m_conv": i["m_conv"], "m": i["m"], "cg_iters_max": i["cg_iters_max"],
+                       "max_true_resid": max(i["true_resid"]), "ms_lanczos": i["ms_lanczos"],
+                       "ms_po": i["ms_po"]} for i in infos],
+           "ms_cg_batched": infos[0]["ms_cg"], "clocks": clocks,
+           "gpu_launches": seedcg.seedcg_kernel_launches() - l0}
+    print(json.dumps(out))
+    for s in solvers:
+        s.close()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -416,6 +468,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif len(__import__("paper_0901_3512_gb300.workloads", fromlist=["W"]).WORKLOADS[args.workload].fields) > 1:
+        run_batch(args)
     else:
         run_ours(args)
 

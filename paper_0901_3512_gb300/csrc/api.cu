@@ -141,19 +141,19 @@ seedcg_status seedcg_solve(seedcg_handle* h, int nrhs, const double* B, double* 
         SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
         const size_t bytes = (size_t)nrhs * h->g.vol * 12 * sizeof(double2);
         const bool bd = is_device_ptr(B), xd = is_device_ptr(X);
-        seedcg::DevBuf hb, hx;
+        // device copies of host B / X live in the handle (kept between solves)
+        if (!bd || !xd) h->hostio.ensure(2 * bytes + 512);
         const double* Bd = B;
         double* Xd = X;
         if (!bd) {
-            hb.ensure(bytes);
-            SEEDCG_CUDA_TRY(cudaMemcpyAsync(hb.p, B, bytes, cudaMemcpyHostToDevice, st));
-            Bd = hb.as<double>();
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(h->hostio.p, B, bytes, cudaMemcpyHostToDevice, st));
+            Bd = h->hostio.as<double>();
         }
         if (!xd) {
-            hx.ensure(bytes);
+            double* hx = h->hostio.as<double>() + 2 * (bytes / sizeof(double2));
             if (h->opt.x0_given)
-                SEEDCG_CUDA_TRY(cudaMemcpyAsync(hx.p, X, bytes, cudaMemcpyHostToDevice, st));
-            Xd = hx.as<double>();
+                SEEDCG_CUDA_TRY(cudaMemcpyAsync(hx, X, bytes, cudaMemcpyHostToDevice, st));
+            Xd = hx;
         }
         seedcg_status code = seedcg::solve_impl(h, nrhs, Bd, Xd, tol, extra_iters, reorth_period,
                                                 info, st);
@@ -528,6 +528,7 @@ void seedcg_destroy(seedcg_handle* h) {
     h->coef.release();
     h->tcbuf.release();
     h->cgbuf.release();
+    h->hostio.release();
     seedcg::guess_free(h);
     h->staging.release();
     if (h->pinned) cudaFreeHost(h->pinned);

@@ -25,6 +25,7 @@ struct seedcg_handle {
     seedcg::DevBuf staging;       // complex128 staging of host B / X
     seedcg::DevBuf tcbuf;         // tensor-core projection: bf16 B operand + FP32 partials
     seedcg::DevBuf cgbuf;         // batched CG engine workspace
+    seedcg::DevBuf hostio;        // device copies of host B / X passed to seedcg_solve
     std::vector<double> alpha, beta, delta;  // Lanczos scalars of the last solve
     int last_m = 0;
     int last_m_conv = 0, last_po_count = 0, last_lz_status = 0;
