@@ -157,6 +157,28 @@ seedcg_status seedcg_apply(seedcg_handle* h, int op, int prec, int multi, int n,
                            const double* in, double* out, void* stream);
 
 /*
+ * seedcg_apply for callers that cannot allocate device memory, e.g. a host
+ * framework whose caching allocator has reserved the GPU's memory for its own
+ * pool, or a caller that cannot afford the allocation and implicit
+ * synchronisation of cudaMalloc / cudaFree on every call.  (The paper has no
+ * counterpart: this is a property of the library, not of the method.)
+ * Same arguments, layouts and results as seedcg_apply; in and out are the
+ * caller's device buffers.  The scratch (internal copies of in, the
+ * intermediate and the output) is one fixed 16 MiB device array that every
+ * GPU loading this library holds until the process exits; the call returns
+ * SEEDCG_ERR_ARG, with a message, when 3 * n * V * 12 * (16 B for prec 0,
+ * 8 B for prec 1) exceeds 16 MiB.  No device memory is allocated or freed.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and every call
+ * overwrites it before reading it: calls that overlap on the GPU (other
+ * streams, other threads, other handles on the same device) race.
+ */
+seedcg_status seedcg_apply_noalloc(seedcg_handle* h, int op, int prec, int multi, int n,
+                                   const double* in, double* out, void* stream);
+
+/*
+ * After a solve: copy the Lanczos scalars of RHS 1/*
  * After a solve: copy the Lanczos scalars of RHS 1 (alpha_1..m, beta_1..m,
  * delta_1..m; Eq. 2) into caller host arrays of `cap` doubles (any may be
  * NULL).  Returns the number m written via *m_out.

@@ -499,6 +499,16 @@ void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n
                      const float2* in, float2* out, cudaStream_t s) {
     launch_dslash_mrhs<float>(g, u, kappa, dag, n, in, out, s);
 }
+void dslash_mrhs_fixed_f64(const Geom& g, const double2* u, double kappa, int dag, int n,
+                           const double2* in, double2* out, cudaStream_t s) {
+    const BrickChoice c{128, 0};
+    launch_dslash_mrhs<double>(g, u, kappa, dag, n, in, out, s, nullptr, nullptr, nullptr, &c);
+}
+void dslash_mrhs_fixed_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
+                           const float2* in, float2* out, cudaStream_t s) {
+    const BrickChoice c{128, 0};
+    launch_dslash_mrhs<float>(g, u, kappa, dag, n, in, out, s, nullptr, nullptr, nullptr, &c);
+}
 bool dslash_dot_supported(const Geom& g) {
     Brick br;
     return make_brick(g, br) && (br.tb == 64 || br.tb == 96 || br.tb == 128);

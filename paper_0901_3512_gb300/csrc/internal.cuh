@@ -144,6 +144,12 @@ void dslash_mrhs_f64(const Geom& g, const double2* u, double kappa, int dag, int
 void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                      const float2* in, float2* out, cudaStream_t s);
 
+// the multi-RHS kernel with its default tile shape, never timing alternatives
+void dslash_mrhs_fixed_f64(const Geom& g, const double2* u, double kappa, int dag, int n,
+                           const double2* in, double2* out, cudaStream_t s);
+void dslash_mrhs_fixed_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
+                           const float2* in, float2* out, cudaStream_t s);
+
 // D^dag on n fields fused with the CG step-length dot: part[r][b] receives block
 // b's share of Re p_r^dag (D^dag in_r); needs a brick-tiled lattice
 bool dslash_dot_supported(const Geom& g);

@@ -60,7 +60,7 @@ EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "see
            "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
            "seedcg_project_basis", "seedcg_batch_solve", "seedcg_guess_set_weights",
            "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
-           "seedcg_guess_predict"]
+           "seedcg_guess_predict", "seedcg_apply_noalloc"]
 GUESS_NW = 11520
 
 
@@ -101,6 +101,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         vp, vp, vp]
+    lib.seedcg_apply_noalloc.restype = ctypes.c_int
     lib.seedcg_guess_set_weights.argtypes = [vp, vp]
     lib.seedcg_guess_get_weights.argtypes = [vp, vp]
     lib.seedcg_guess_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, dp, vp, vp]
@@ -236,6 +239,16 @@ def seedcg_apply(h, op: int, prec: int, multi: int, n: int, inp, out, stream=Non
     _check(h, load().seedcg_apply(h, int(op), int(prec), int(multi), int(n),
                                   ctypes.c_void_p(_ptr(inp)), ctypes.c_void_p(_ptr(out)),
                                   _stream_ptr(stream)))
+
+
+def seedcg_apply_noalloc(h, op: int, prec: int, multi: int, n: int, inp, out, stream=None):
+    """seedcg_apply without any device allocation (fixed 16 MiB scratch)."""
+    _check(h, load().seedcg_apply_noalloc(h, int(op), int(prec), int(multi), int(n),
+                                          ctypes.c_void_p(_ptr(inp)), ctypes.c_void_p(_ptr(out)),
+                                          _stream_ptr(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def seedcg_get_lanczos(h, cap: int):
