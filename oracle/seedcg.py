@@ -156,10 +156,21 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
             eta[j - 1] = np.vdot(v, R0[j]) - g * eta[j - 1]
             X[j] = X[j] + eta[j - 1] * w
         eta_hist[:, k0] = eta
-        # Step 8: periodic re-orthogonalisation
+        # Step 8: periodic re-orthogonalisation.  The paper is silent on a PO
+        # step that finds v_i mostly inside span(v_1..v_{i-1}) (the basis lost
+        # orthogonality beyond repair between two PO steps, or the Krylov space
+        # is exhausted).  Reading: the run ends at i - 1 when a projection
+        # pass leaves ||v_i|| < 1/2, or when re-orthogonalising lengthens f
+        # (an orthogonal projection never does); the systems then go to CG.
         if reorth_period > 0 and i % reorth_period == 0:
+            beta_pre = _norm(f)
+            v_po, f_po, ok = periodic_reorth(V, i, v, f, po_passes, guard=True)
+            if not ok or not (_norm(f_po) <= 1.01 * beta_pre):
+                breakdown = True
+                i -= 1
+                break
             po_count += 1
-            v, f = periodic_reorth(V, i, v, f, po_passes)
+            v, f = v_po, f_po
         V[k0] = v
         # Step 9: finish the iteration
         beta[k0] = _norm(f)
@@ -183,22 +194,27 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
                              breakdown, hist)
 
 
-def periodic_reorth(V: np.ndarray, i: int, v: np.ndarray, f: np.ndarray, passes: int = 1):
+def periodic_reorth(V: np.ndarray, i: int, v: np.ndarray, f: np.ndarray, passes: int = 1,
+                    guard: bool = False):
     """Step 8 of Algorithm 1 at iteration i (1-based), classical Gram-Schmidt.
 
     V holds v_1..v_{i-1} in rows 0..i-2.  Re-orthonormalise v_i against
     v_1..v_{i-1}; then re-orthogonalise f (the un-normalised v_{i+1}) against
     v_1..v_i, v_i being the new one.  Row i-1 of V receives the new v_i.
+    With guard=True the result is (v, f, ok): ok is False, and V is left
+    untouched, when a pass leaves ||v|| below 1/2 (v_i was a unit vector).
     """
     prev = V[:i - 1]
     for _ in range(passes):
         v = v - (prev.conj() @ v) @ prev
+        if guard and not (_norm(v) >= 0.5):
+            return v, f, False
     v = v / _norm(v)
     V[i - 1] = v
     upto = V[:i]
     for _ in range(passes):
         f = f - (upto.conj() @ f) @ upto
-    return v, f
+    return (v, f, True) if guard else (v, f)
 
 
 # ---------------------------------------------------------------------------

@@ -243,3 +243,45 @@ def test_step8_reorth_against_every_previous_vector(passes):
     # v2 is (z's part outside span V_{i-1}) normalised: the only admissible result
     zp = z - (V[:i - 1].conj() @ z) @ V[:i - 1]
     assert np.linalg.norm(v2 - zp / np.linalg.norm(zp)) < 1e-13
+
+
+def _near_critical(nrhs=2):
+    """4^4, eps 0.5, kappa 0.23: cond(M) ~ 4e4 with a few isolated low modes
+    (dense spectrum: lambda_2 / lambda_1 ~ 1.9, lambda_8 / lambda_1 ~ 9), the
+    near-critical regime of the paper's example (Section 3)."""
+    dims = (4, 4, 4, 4)
+    op = WilsonOperator(dims, W.gauge_field(dims, 0.5, 7), 0.23)
+    eta = W.point_sources(dims, nrhs).reshape(nrhs, -1)
+    return op, np.stack([op.Ddag(e) for e in eta])
+
+
+def test_seeding_gain_near_critical():
+    """Section 3: the seeded second system needs far fewer CG iterations
+    (matvecs) than CG from zero, and running RHS 1 further past convergence
+    does not make it worse."""
+    op, B = _near_critical()
+    plain = cg(op.M, B[1], None, 1e-8, 20000).iters
+    r12 = improved_seed_cg(op.M, B, None, 1e-8, 20000, 10, past_factor=1.2)
+    r20 = improved_seed_cg(op.M, B, None, 1e-8, 20000, 10, past_factor=2.0)
+    assert r20.seed.m == math.ceil(2.0 * r20.seed.m_conv)
+    assert r20.cg_iters[1] < 0.4 * plain
+    assert r20.cg_iters[1] <= r12.cg_iters[1] < plain
+    assert max(r12.true_resid.max(), r20.true_resid.max()) <= 1e-8
+
+
+def test_po_guard_when_orthogonality_is_lost_between_po_steps():
+    """With k = 100 on N = 3072 the basis loses orthogonality between PO
+    steps; a PO step then lengthens f (impossible for an orthogonal
+    projection) and the guard of step 8 ends Lanczos at i - 1, i a multiple of
+    k.  The stored basis is then far from orthonormal, which is what the
+    guard detects, and CG still brings every system to tol."""
+    op, B = _near_critical(3)
+    r = improved_seed_cg(op.M, B, None, 1e-8, 20000, 100, past_factor=2.0)
+    s = r.seed
+    assert s.breakdown and s.m % 100 == 99 and s.po_count == (s.m + 1) // 100 - 1
+    V = s.V
+    assert np.abs(V.conj() @ V.T - np.eye(len(V))).max() > 0.1
+    assert np.all(np.isfinite(r.X)) and r.true_resid.max() <= 1e-8
+    # the guard never fires while PO keeps the basis orthonormal (k = 10)
+    r10 = improved_seed_cg(op.M, B[:2], None, 1e-8, 20000, 10, past_factor=1.0)
+    assert not r10.seed.breakdown and r10.seed.m == r10.seed.m_conv
