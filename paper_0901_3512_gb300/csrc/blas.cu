@@ -154,8 +154,13 @@ k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__
 template <typename R, typename VT, int NV, int RPW, int CHUNK>
 __global__ void __launch_bounds__(256)
 k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __restrict__ X,
-               long ldx, int nv, long n, int chunk, double2* __restrict__ part) {
-    __shared__ cx_t<R> sx[NV][CHUNK];
+               long ldx, int nv, long n, int chunk, int rg, double2* __restrict__ part) {
+    // block (x, y): one chunk of entries (X chunk staged in shared memory)
+    // against the rows of group y (rg rows); warp: RPW rows at a time; lane: W
+    // consecutive entries per 16-byte load.  chunk and n are multiples of W
+    // (host-checked).
+    constexpr int W = VLoad<R, VT>::N;
+    __shared__ __align__(16) cx_t<R> sx[NV][CHUNK];
     const long e0 = (long)blockIdx.x * chunk;
     const int cnt = (int)(n - e0 < chunk ? n - e0 : chunk);
     for (int k = threadIdx.x; k < NV * chunk; k += blockDim.x) {
@@ -165,7 +170,8 @@ k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __rest
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     double2* out = part + (size_t)blockIdx.x * na * NV;
-    for (int a0 = warp * RPW; a0 < na; a0 += nw * RPW) {
+    const int rbeg = blockIdx.y * rg, rend = rbeg + rg < na ? rbeg + rg : na;
+    for (int a0 = rbeg + warp * RPW; a0 < rend; a0 += nw * RPW) {
         cx_t<R> acc[RPW][NV];
 #pragma unroll
         for (int r = 0; r < RPW; r++)
@@ -173,17 +179,20 @@ k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __rest
             for (int j = 0; j < NV; j++) acc[r][j] = mk<R>(0, 0);
         const VT* rows[RPW];
 #pragma unroll
-        for (int r = 0; r < RPW; r++) rows[r] = V + (size_t)(a0 + r < na ? a0 + r : a0) * ldv + e0;
-#pragma unroll 4
-        for (int e = lane; e < cnt; e += 32) {
-            cx_t<R> xv[NV];
+        for (int r = 0; r < RPW; r++) rows[r] = V + (size_t)(a0 + r < rend ? a0 + r : a0) * ldv + e0;
+#pragma unroll 2
+        for (int e = lane * W; e < cnt; e += 32 * W) {
+            cx_t<R> a[RPW][W];
 #pragma unroll
-            for (int j = 0; j < NV; j++) xv[j] = sx[j][e];
+            for (int r = 0; r < RPW; r++) VLoad<R, VT>::get(rows[r] + e, a[r]);
 #pragma unroll
-            for (int r = 0; r < RPW; r++) {
-                const cx_t<R> a = ld_cx<R>(rows[r], e);
+            for (int w = 0; w < W; w++) {
 #pragma unroll
-                for (int j = 0; j < NV; j++) acc[r][j] = cfma_conj(a, xv[j], acc[r][j]);
+                for (int j = 0; j < NV; j++) {
+                    const cx_t<R> xv = sx[j][e + w];
+#pragma unroll
+                    for (int r = 0; r < RPW; r++) acc[r][j] = cfma_conj(a[r][w], xv, acc[r][j]);
+                }
             }
         }
 #pragma unroll
@@ -192,7 +201,7 @@ k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __rest
             for (int j = 0; j < NV; j++) {
                 double re = warp_sum((double)acc[r][j].x);
                 double im = warp_sum((double)acc[r][j].y);
-                if (lane == 0 && a0 + r < na && j < nv)
+                if (lane == 0 && a0 + r < rend && j < nv)
                     out[(size_t)(a0 + r) * NV + j] = make_double2(re, im);
             }
         }
@@ -300,7 +309,7 @@ template <typename R, int NV> constexpr int proj_chunk() { return 32768 / (NV * 
 // entries per block: enough blocks to fill 152 SMs twice, at most the staging capacity
 inline int proj_chunk_for(long n, int cap) {
     long c = (n + 303) / 304;
-    c = (c + 31) / 32 * 32;
+    c = (c + 127) / 128 * 128;   // whole 16-byte vectors per lane
     if (c < 256) c = 256;
     if (c > cap) c = cap;
     return (int)c;
@@ -318,6 +327,9 @@ template <typename R, typename AT>
 void proj(const AT* A, long lda, int na, const cx_t<R>* X, long ldx, int nx, long n, double2* C,
           int ldc, double2* scratch, size_t scratch_elems, cudaStream_t s) {
     if (na <= 0 || nx <= 0) return;
+    constexpr int W = 16 / (int)sizeof(AT);
+    if (n % W != 0 || lda % W != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)
+        throw Error{SEEDCG_ERR_ARG, "proj: basis rows must be 16-byte aligned whole vectors"};
     for (int c0 = 0; c0 < nx; c0 += 4) {
         const int nv = nx - c0 < 4 ? nx - c0 : 4;
         const cx_t<R>* Xc = X + (size_t)c0 * ldx;
@@ -326,7 +338,9 @@ void proj(const AT* A, long lda, int na, const cx_t<R>* X, long ldx, int nx, lon
             const int ch = proj_chunk_for(n, CH);
             const int nblk = (int)((n + ch - 1) / ch);
             if ((size_t)nblk * na * 2 > scratch_elems) throw Error{SEEDCG_ERR_OOM, "proj scratch"};
-            k_proj_partial<R, AT, 2, 2, CH><<<nblk, 256, 0, s>>>(A, lda, na, Xc, ldx, nv, n, ch, scratch);
+            constexpr int RG = 8 * 4 * 4;
+            k_proj_partial<R, AT, 2, 4, CH><<<dim3(nblk, (na + RG - 1) / RG), 256, 0, s>>>(
+                A, lda, na, Xc, ldx, nv, n, ch, RG, scratch);
             SEEDCG_CHECK_LAUNCH();
             k_proj_reduce<2><<<(na * nv + 7) / 8, 256, 0, s>>>(scratch, nblk, na, nv, C, ldc, c0);
         } else {
@@ -334,7 +348,9 @@ void proj(const AT* A, long lda, int na, const cx_t<R>* X, long ldx, int nx, lon
             const int ch = proj_chunk_for(n, CH);
             const int nblk = (int)((n + ch - 1) / ch);
             if ((size_t)nblk * na * 4 > scratch_elems) throw Error{SEEDCG_ERR_OOM, "proj scratch"};
-            k_proj_partial<R, AT, 4, 1, CH><<<nblk, 256, 0, s>>>(A, lda, na, Xc, ldx, nv, n, ch, scratch);
+            constexpr int RG = 8 * 2 * 4;
+            k_proj_partial<R, AT, 4, 2, CH><<<dim3(nblk, (na + RG - 1) / RG), 256, 0, s>>>(
+                A, lda, na, Xc, ldx, nv, n, ch, RG, scratch);
             SEEDCG_CHECK_LAUNCH();
             k_proj_reduce<4><<<(na * nv + 7) / 8, 256, 0, s>>>(scratch, nblk, na, nv, C, ldc, c0);
         }

@@ -101,4 +101,39 @@ __device__ __forceinline__ void st_cx(__nv_bfloat162* p, size_t i, double2 z) {
     p[i] = __float22bfloat162_rn(make_float2((float)z.x, (float)z.y));
 }
 
+// One 16-byte load of consecutive complex elements of type VT (1 double2,
+// 2 float2 or 4 bf16x2), widened to cx_t<R>; marked streaming (evict-first):
+// the stored basis is read once per use and should not push the iteration
+// vectors out of L2.  p must be 16-byte aligned.
+template <typename R, typename VT> struct VLoad;
+template <typename R> struct VLoad<R, double2> {
+    static constexpr int N = 1;
+    __device__ __forceinline__ static void get(const double2* p, cx_t<R> (&o)[1]) {
+        const double2 z = __ldcs(p);
+        o[0] = mk<R>((R)z.x, (R)z.y);
+    }
+};
+template <typename R> struct VLoad<R, float2> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void get(const float2* p, cx_t<R> (&o)[2]) {
+        const float4 z = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = mk<R>((R)z.x, (R)z.y);
+        o[1] = mk<R>((R)z.z, (R)z.w);
+    }
+};
+template <typename R> struct VLoad<R, __nv_bfloat162> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void get(const __nv_bfloat162* p, cx_t<R> (&o)[4]) {
+        const uint4 z = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __nv_bfloat162 b;
+            memcpy(&b, &w[k], 4);
+            const float2 f = __bfloat1622float2(b);
+            o[k] = mk<R>((R)f.x, (R)f.y);
+        }
+    }
+};
+
 }  // namespace seedcg

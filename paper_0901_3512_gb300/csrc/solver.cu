@@ -31,6 +31,15 @@ inline int red_blocks(long n) {
     return (int)std::min<long>(b, 152 * 8);
 }
 
+// blocks for a kernel whose thread handles one 16-byte group of entries (n / w
+// groups), in equal rounds of at most kMaxRedBlocks blocks
+inline int vec_blocks(long n, int w) {
+    long b = (n / w + kRedThreads - 1) / kRedThreads;
+    if (b < 1) b = 1;
+    const long rounds = (b + kMaxRedBlocks - 1) / kMaxRedBlocks;
+    return (int)((b + rounds - 1) / rounds);
+}
+
 inline int site_blocks(int vol) { return (vol + kRedThreads - 1) / kRedThreads; }
 
 // ===========================================================================
@@ -235,55 +244,137 @@ k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __r
 // ---- step 8: periodic re-orthogonalisation (classical Gram-Schmidt) ----
 // [v, f] -= V_{1:i-1} c   with c = V^dag [v, f] already in coef (double2 [i-1][2]);
 // the columns of coef follow the order of the two rows passed to gemm_t.
+
+// av, af (W entries from e) += sum over rows [r0, r1) of V[a][e..] * c[a][0 / 1]:
+// one 16-byte load per row and thread, coefficients of 256 rows at a time in
+// shared memory.  Every thread of the block calls it (it synchronises);
+// `live` marks threads that own entries.
+template <typename R, typename VT>
+__device__ __forceinline__ void po_accumulate(const VT* __restrict__ V, long ldv, int r0, int r1,
+                                              const double2* __restrict__ coef, int cv, long e,
+                                              bool live, cx_t<R> (&av)[VLoad<R, VT>::N],
+                                              cx_t<R> (&af)[VLoad<R, VT>::N],
+                                              cx_t<R> (*sc)[2]) {
+    constexpr int W = VLoad<R, VT>::N;
+    constexpr int CH = 256;
+#pragma unroll
+    for (int w = 0; w < W; w++) av[w] = af[w] = mk<R>(0, 0);
+    for (int a0 = r0; a0 < r1; a0 += CH) {
+        const int cnt = r1 - a0 < CH ? r1 - a0 : CH;
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * CH; k += blockDim.x) {
+            int a = k >> 1, c = k & 1;
+            double2 z = a < cnt ? coef[(size_t)(a0 + a) * 2 + (c == 0 ? cv : 1 - cv)]
+                                : make_double2(0.0, 0.0);
+            sc[a][c] = mk<R>((R)z.x, (R)z.y);
+        }
+        __syncthreads();
+        if (live) {
+            const VT* col = V + (size_t)a0 * ldv + e;
+#pragma unroll 8
+            for (int a = 0; a < cnt; a++) {
+                cx_t<R> x[W];
+                VLoad<R, VT>::get(col + (size_t)a * ldv, x);
+                const cx_t<R> c0 = sc[a][0], c1 = sc[a][1];
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    av[w] = cfma(x[w], c0, av[w]);
+                    af[w] = cfma(x[w], c1, af[w]);
+                }
+            }
+        }
+    }
+}
+
+// after the subtraction: ||v_i|| decides whether the run goes on
+__device__ __forceinline__ void po_check_nv(const LzDev& L, int i, double nv2) {
+    const double nv = sqrt(nv2);
+    L.ctl->nv = nv;
+    // v_i is a unit vector; if the projection removed most of it the basis no
+    // longer spans what the recurrence assumes (numerical invariant subspace or
+    // a basis stored too coarsely): end the run at i - 1, before this vector.
+    if (!(nv >= 0.5)) {
+        L.ctl->breakdown = 2;
+        L.ctl->m = i - 1;
+    }
+}
+
+// the whole subtraction in one pass: thread = W consecutive entries down all rows
+// (n is a multiple of W, host-checked)
 template <typename R, typename VT>
 __global__ void __launch_bounds__(kRedThreads)
 k_po_sub(const VT* __restrict__ V, long ldv, int na, const double2* __restrict__ coef, int cv,
          cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int i, LzDev L) {
     if (i > L.ctl->m) return;
-    constexpr int CH = 128;
-    __shared__ cx_t<R> sc[CH][2];
+    constexpr int W = VLoad<R, VT>::N;
+    __shared__ cx_t<R> sc[256][2];
     R part = 0;
-    for (long base = blockIdx.x * (long)blockDim.x; base < n; base += (long)gridDim.x * blockDim.x) {
-        const long e = base + threadIdx.x;
-        cx_t<R> av = mk<R>(0, 0), af = mk<R>(0, 0);
-        for (int a0 = 0; a0 < na; a0 += CH) {
-            const int cnt = na - a0 < CH ? na - a0 : CH;
-            __syncthreads();
-            for (int k = threadIdx.x; k < 2 * CH; k += blockDim.x) {
-                int a = k >> 1, c = k & 1;
-                double2 z = a < cnt ? coef[(size_t)(a0 + a) * 2 + (c == 0 ? cv : 1 - cv)]
-                                    : make_double2(0.0, 0.0);
-                sc[a][c] = mk<R>((R)z.x, (R)z.y);
+    const long ng = n / W;
+    for (long g0 = blockIdx.x * (long)blockDim.x; g0 < ng; g0 += (long)gridDim.x * blockDim.x) {
+        const long g = g0 + threadIdx.x;
+        const long e = g * W;
+        cx_t<R> av[W], af[W];
+        po_accumulate<R, VT>(V, ldv, 0, na, coef, cv, e, g < ng, av, af, sc);
+        if (g < ng) {
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                const cx_t<R> vv = csub(v[e + w], av[w]);
+                v[e + w] = vv;
+                f[e + w] = csub(f[e + w], af[w]);
+                part += vv.x * vv.x + vv.y * vv.y;
             }
-            __syncthreads();
-            if (e < n) {
-#pragma unroll 8
-                for (int a = 0; a < cnt; a++) {
-                    cx_t<R> x = ld_cx<R>(V, (size_t)(a0 + a) * ldv + e);
-                    av = cfma(x, sc[a][0], av);
-                    af = cfma(x, sc[a][1], af);
-                }
-            }
-        }
-        if (e < n) {
-            cx_t<R> vv = csub(v[e], av);
-            v[e] = vv;
-            f[e] = csub(f[e], af);
-            part += vv.x * vv.x + vv.y * vv.y;
         }
     }
     double red[1] = {(double)part};
-    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) {
-        const double nv = sqrt(tot[0]);
-        L.ctl->nv = nv;
-        // v_i is a unit vector; if the projection removed most of it the basis no
-        // longer spans what the recurrence assumes (numerical invariant subspace or
-        // a basis stored too coarsely): end the run at i - 1, before this vector.
-        if (!(nv >= 0.5)) {
-            L.ctl->breakdown = 2;
-            L.ctl->m = i - 1;
+    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) { po_check_nv(L, i, tot[0]); });
+}
+
+// the subtraction split over row segments (blockIdx.y = segment of `seg` rows)
+// so that long bases fill the GPU in many even waves: segment s writes its sums
+// to part[s][0 / 1][n]; k_po_sub_fin adds the segments in a fixed order.
+template <typename R, typename VT>
+__global__ void __launch_bounds__(kRedThreads)
+k_po_sub_seg(const VT* __restrict__ V, long ldv, int na, int seg, const double2* __restrict__ coef,
+             int cv, long n, cx_t<R>* __restrict__ part, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    constexpr int W = VLoad<R, VT>::N;
+    __shared__ cx_t<R> sc[256][2];
+    const long g = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const bool live = g < n / W;
+    const long e = g * W;
+    const int r0 = blockIdx.y * seg, r1 = r0 + seg < na ? r0 + seg : na;
+    cx_t<R> av[W], af[W];
+    po_accumulate<R, VT>(V, ldv, r0, r1, coef, cv, e, live, av, af, sc);
+    if (live) {
+        cx_t<R>* pv = part + (size_t)blockIdx.y * 2 * n + e;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            pv[w] = av[w];
+            pv[n + w] = af[w];
         }
-    });
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads)
+k_po_sub_fin(const cx_t<R>* __restrict__ part, int nseg, cx_t<R>* __restrict__ v,
+             cx_t<R>* __restrict__ f, long n, int i, LzDev L) {
+    if (i > L.ctl->m) return;
+    R acc = 0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+         e += (long)gridDim.x * blockDim.x) {
+        cx_t<R> sv = part[e], sf = part[n + e];
+        for (int s = 1; s < nseg; s++) {
+            sv = cadd(sv, part[(size_t)s * 2 * n + e]);
+            sf = cadd(sf, part[(size_t)s * 2 * n + n + e]);
+        }
+        const cx_t<R> vv = csub(v[e], sv);
+        v[e] = vv;
+        f[e] = csub(f[e], sf);
+        acc += vv.x * vv.x + vv.y * vv.y;
+    }
+    double red[1] = {(double)acc};
+    grid_sum<1>(red, L.partials, L.counters + CTR_PO2, [&](double* tot) { po_check_nv(L, i, tot[0]); });
 }
 
 // v_i /= ||v_i||; dvf = v_i^dag f
@@ -571,6 +662,40 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
             gemm_t<R, VT>(Vb, n, rows, X, n, nvec, n, Cc, ldc, split, split_elems, st);
     };
 
+    // [v, f] -= V c: one pass down all rows, or (long bases) row segments so
+    // that the grid is many even waves, summed by k_po_sub_fin
+    int nsm = 0;
+    SEEDCG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    static int seg_occ = 0;
+    if (!seg_occ)
+        SEEDCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&seg_occ, k_po_sub_seg<R, VT>,
+                                                                      kRedThreads, 0));
+    constexpr int kW = 16 / (int)sizeof(VT);
+    if (n % 4 != 0) throw Error{SEEDCG_ERR_ARG, "spinor length not a multiple of 4"};
+    const long po_gb = (n / kW + kRedThreads - 1) / kRedThreads;
+    const long seg_cap = (long)(split_elems * sizeof(double2) / (2 * (size_t)n * sizeof(cx_t<R>)));
+    auto po_subtract = [&](int na, int cvcol, cx_t<R>* vv, cx_t<R>* ff, int i) {
+        long nseg = 1;
+        if (na >= 256) {
+            const long resident = (long)nsm * std::max(seg_occ, 1);
+            nseg = std::min<long>({8, (6 * resident + po_gb - 1) / po_gb, na / 128, seg_cap});
+        }
+        if (nseg <= 1) {
+            k_po_sub<R, VT><<<vec_blocks(n, kW), kRedThreads, 0, st>>>(Vb, n, na, Cc, cvcol, vv, ff, n,
+                                                                       i, L);
+            SEEDCG_CHECK_LAUNCH();
+            return;
+        }
+        const int seg = (int)((na + nseg - 1) / nseg);
+        const int ns = (na + seg - 1) / seg;
+        cx_t<R>* sp = reinterpret_cast<cx_t<R>*>(split);
+        k_po_sub_seg<R, VT><<<dim3((unsigned)po_gb, ns), kRedThreads, 0, st>>>(Vb, n, na, seg, Cc, cvcol,
+                                                                              n, sp, i, L);
+        SEEDCG_CHECK_LAUNCH();
+        k_po_sub_fin<R><<<rb, kRedThreads, 0, st>>>(sp, ns, vv, ff, n, i, L);
+        SEEDCG_CHECK_LAUNCH();
+    };
+
     int* pin = reinterpret_cast<int*>(h->pinned);
     double* pind = reinterpret_cast<double*>(pin + 2048);
     pin[1024] = 0;
@@ -655,8 +780,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
                 const int cvcol = (v == vA) ? 0 : 1;
                 for (int pass = 0; pass < std::max(o.po_passes, 1); pass++) {
                     project(na, Bst, 2, 2);
-                    k_po_sub<R, VT><<<rb, kRedThreads, 0, st>>>(Vb, n, na, Cc, cvcol, v, fv, n, i, L);
-                    SEEDCG_CHECK_LAUNCH();
+                    po_subtract(na, cvcol, v, fv, i);
                 }
                 k_po_normalise<R><<<rb, kRedThreads, 0, st>>>(v, fv, n, i, L);
                 SEEDCG_CHECK_LAUNCH();
