@@ -51,6 +51,9 @@ def _args():
                    help="write this run's work units (m, CG iterations) for the reference arm")
     p.add_argument("--compare-fp64", action="store_true",
                    help="also time one plain FP64 solve of the same workload (slow)")
+    p.add_argument("--tc-po", type=int, default=1, choices=[0, 1, 2],
+                   help="with --only po: use_tensor_cores for the bf16 basis (0 SIMT, 1 default: "
+                        "tcgen05 for the seeds only, 2 tcgen05 for the PO projection too)")
     p.add_argument("--only", default=None, choices=["dslash", "po"],
                    help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
                         "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
@@ -454,7 +457,7 @@ def run_only(args):
         s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
         X = torch.zeros_like(B)
         s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max,
-                      stop_after_seed=1)
+                      stop_after_seed=1, use_tensor_cores=args.tc_po)
         code, info = s.solve(B, X, wl.tol, 0, wl.reorth_period, allow_not_converged=True)
         print(json.dumps({"only": "po", "m": info["m"], "ms_po": info["ms_po"],
                           "po_count": info["po_count"]}))

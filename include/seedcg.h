@@ -76,7 +76,11 @@ typedef struct {
     int cg_maxiter;        /* CG iteration cap per system (default 20000)               */
     int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */
     int poll_every;        /* iterations between host polls of device flags (default 32) */
-    int use_tensor_cores;  /* 1: bf16-basis projections V^dag X on tcgen05 (default), 0: SIMT */
+    int use_tensor_cores;  /* bf16 basis only: 1 (default) projections V^dag X of more than
+                              two vectors (the Eq. (1) seeds) on tcgen05 and the
+                              two-vector PO projection on SIMT (measured faster: it is a
+                              bandwidth-bound GEMV); 2: every projection on tcgen05;
+                              0: every projection on SIMT */
     int use_guess;         /* 1: start every system from the learned guess x_0 = net(b)
                               (weights set by seedcg_guess_set_weights/_train); a system
                               whose guess has ||b - M x_0|| >= ||b|| starts from 0 */

@@ -46,7 +46,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.seed_mode == 0 && o.precision != SEEDCG_FP64) { why = "literal seeding (seed_mode 0) needs precision FP64"; return false; }
     if (o.cg_maxiter < 1) { why = "cg_maxiter must be >= 1"; return false; }
     if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
-    if (o.use_tensor_cores < 0 || o.use_tensor_cores > 1) { why = "use_tensor_cores must be 0 or 1"; return false; }
+    if (o.use_tensor_cores < 0 || o.use_tensor_cores > 2) { why = "use_tensor_cores must be 0, 1 or 2"; return false; }
     if (o.use_guess < 0 || o.use_guess > 1) { why = "use_guess must be 0 or 1"; return false; }
     return true;
 }

@@ -160,12 +160,14 @@ k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __rest
     // consecutive entries per 16-byte load.  chunk and n are multiples of W
     // (host-checked).
     constexpr int W = VLoad<R, VT>::N;
-    __shared__ __align__(16) cx_t<R> sx[NV][CHUNK];
+    // X chunk in shared memory, component-major: entry e at sx[j][e % W][e / W], so
+    // that the lanes of a warp (W consecutive entries each) read consecutive words
+    __shared__ __align__(16) cx_t<R> sx[NV][W][CHUNK / W];
     const long e0 = (long)blockIdx.x * chunk;
     const int cnt = (int)(n - e0 < chunk ? n - e0 : chunk);
     for (int k = threadIdx.x; k < NV * chunk; k += blockDim.x) {
         const int j = k / chunk, e = k % chunk;
-        sx[j][e] = (j < nv && e < cnt) ? X[(size_t)j * ldx + e0 + e] : mk<R>(0, 0);
+        sx[j][e % W][e / W] = (j < nv && e < cnt) ? X[(size_t)j * ldx + e0 + e] : mk<R>(0, 0);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -189,20 +191,26 @@ k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __rest
             for (int w = 0; w < W; w++) {
 #pragma unroll
                 for (int j = 0; j < NV; j++) {
-                    const cx_t<R> xv = sx[j][e + w];
+                    const cx_t<R> xv = sx[j][w][e / W];
 #pragma unroll
                     for (int r = 0; r < RPW; r++) acc[r][j] = cfma_conj(a[r][w], xv, acc[r][j]);
                 }
             }
         }
+        // lane sums -> warp sum in the working precision (FP64 arithmetic is a
+        // scarce pipe on this GPU; the partials over blocks are summed in FP64)
 #pragma unroll
         for (int r = 0; r < RPW; r++) {
 #pragma unroll
             for (int j = 0; j < NV; j++) {
-                double re = warp_sum((double)acc[r][j].x);
-                double im = warp_sum((double)acc[r][j].y);
+                R re = acc[r][j].x, im = acc[r][j].y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    re += __shfl_down_sync(0xffffffffu, re, o);
+                    im += __shfl_down_sync(0xffffffffu, im, o);
+                }
                 if (lane == 0 && a0 + r < rend && j < nv)
-                    out[(size_t)(a0 + r) * NV + j] = make_double2(re, im);
+                    out[(size_t)(a0 + r) * NV + j] = make_double2((double)re, (double)im);
             }
         }
     }

@@ -650,7 +650,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     }
     auto project = [&](int rows, const cx_t<R>* X, int nvec, int ldc) {
         if constexpr (kBf16) {
-            if (use_tc && nvec <= 32) {
+            if (use_tc && nvec <= 32 && (nvec > 2 || o.use_tensor_cores == 2)) {
                 tc_project(Vb, m_max, rows, reinterpret_cast<const float2*>(X), n, nvec, n, Bm, tpart,
                            tpart_elems, Cc, ldc, &L.ctl->status, st);
                 return;

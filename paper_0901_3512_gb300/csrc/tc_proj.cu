@@ -7,12 +7,14 @@
 //   A = V viewed as bf16 [rows][K = 2N] (each basis vector one row, re/im interleaved),
 //   B = [Re-column, Im-column] per complex vector x: (xr, xi) and (xi, -xr) interleaved,
 //       rounded to bf16, so that D[a][2j] = Re(v_a^dag x_j), D[a][2j+1] = Im(v_a^dag x_j).
-// One CTA owns 128 rows of V and a range of K (split-K); TMA streams 128x64
-// tiles of V and NBx64 tiles of B into a 6-stage shared-memory ring (128-byte
-// swizzle); one thread issues tcgen05.mma (M=128, N=NB, K=16, bf16 -> fp32)
-// into a TMEM accumulator; after the K range four warps read the 128 x NB
-// accumulator back with tcgen05.ld and write FP32 partials, which a second
-// kernel sums over the splits in FP64 (fixed order: deterministic).
+// One CTA owns R tiles of 128 rows of V and a range of K (split-K); per stage
+// TMA streams KC 64-wide K chunks of each of its R row tiles (128x64 boxes)
+// and of B (NBx64 boxes) into a shared-memory ring (128-byte swizzle), so one
+// B chunk serves R row tiles and each row is read in runs of KC x 128 bytes;
+// one thread issues tcgen05.mma (M=128, N=NB, K=16, bf16 -> fp32) into R TMEM
+// accumulators; after the K range four warps read the accumulators back with
+// tcgen05.ld and write FP32 partials, which a second kernel sums over the
+// splits in FP64 (fixed order: deterministic).
 //
 // Every wait on an mbarrier is bounded (1 s of globaltimer); on expiry the
 // kernel records an error code, stops issuing work, waits (bounded) for the
@@ -25,6 +27,8 @@
 #include "tc_proj.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 
 namespace seedcg {
 
@@ -32,8 +36,9 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;          // bf16 elements per 128-byte swizzle row
-constexpr int STAGES = 6;
-constexpr uint32_t A_STAGE_BYTES = BM * BK * 2;  // 16 KB
+constexpr uint32_t A_BOX_BYTES = BM * BK * 2;  // 16 KB
+// shared memory per CTA: two CTAs per SM when a stage is small, one otherwise
+constexpr uint32_t smem_budget(uint32_t stage) { return stage <= 40 * 1024 ? 108 * 1024 : 200 * 1024; }
 constexpr unsigned long long WAIT_NS = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,25 +126,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
-template <int NB>
+template <int NB, int R, int KC>
 struct TcSmem {
-    static constexpr uint32_t B_STAGE = ((NB * BK * 2) + 1023) & ~1023u;
-    static constexpr uint32_t BYTES = STAGES * (A_STAGE_BYTES + B_STAGE) + 1024 + 256;
+    static constexpr uint32_t B_BOX = ((NB * BK * 2) + 1023) & ~1023u;
+    static constexpr uint32_t A_STAGE = R * KC * A_BOX_BYTES;
+    static constexpr uint32_t B_STAGE = KC * B_BOX;
+    static constexpr int STAGES_RAW = (int)(smem_budget(A_STAGE + B_STAGE) / (A_STAGE + B_STAGE));
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+    static_assert(STAGES >= 2, "tensor-core projection stage too large");
+    static constexpr uint32_t BYTES = STAGES * (A_STAGE + B_STAGE) + 1024 + 256;
+    static constexpr uint32_t TMEM_COLS = R * NB <= 32 ? 32 : (R * NB <= 64 ? 64 : (R * NB <= 128 ? 128 : 256));
 };
 
-// NB: columns of B (multiple of 16, <= 64).  part: float [nsplit][rows_valid][NB]
-template <int NB>
+// NB: columns of B (multiple of 16, <= 64).  part: float [nsplit][rows_valid][NB].
+// blockIdx.x = group of R row tiles, blockIdx.y = K split of kb_per_split
+// 64-wide chunks (a multiple of KC).
+template <int NB, int R, int KC>
 __global__ void __launch_bounds__(128, 1)
 k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           int nkb, int kb_per_split, int rows_valid, float* __restrict__ part,
           int* __restrict__ err) {
+    using SM = TcSmem<NB, R, KC>;
+    constexpr int STAGES = SM::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~(uintptr_t)1023);
-    constexpr uint32_t B_STAGE = TcSmem<NB>::B_STAGE;
     uint8_t* sA = smem;
-    uint8_t* sB = smem + STAGES * A_STAGE_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_STAGE);
+    uint8_t* sB = smem + STAGES * SM::A_STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * SM::B_STAGE);
     uint64_t* empty = full + STAGES;
     uint64_t* done = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -147,9 +161,10 @@ k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb0 = blockIdx.y * kb_per_split;
-    const int kb1 = min(kb0 + kb_per_split, nkb);
-    const int nk = kb1 > kb0 ? kb1 - kb0 : 0;
-    constexpr uint32_t TMEM_COLS = NB <= 32 ? 32 : 64;
+    // chunks of this split (past nkb the loads read zeros, so whole stages are fine)
+    const int kb1 = min(kb0 + kb_per_split, ((nkb + KC - 1) / KC) * KC);
+    const int nst = kb1 > kb0 ? (kb1 - kb0) / KC : 0;
+    constexpr uint32_t TMEM_COLS = SM::TMEM_COLS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -171,28 +186,39 @@ k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem_d = *tmem_slot;
+    const int tile0 = blockIdx.x * R;
+    // row tiles of this CTA that hold valid rows (the others are neither loaded nor multiplied)
+    const int tiles_valid = (rows_valid + BM - 1) / BM;
+    const int nt = tiles_valid - tile0 < R ? tiles_valid - tile0 : R;
 
     int issued = 0;  // TMA stages issued by the producer
-    if (nk > 0) {
+    if (nst > 0) {
         if (warp == 0 && lane == 0) {
-            // producer: TMA loads of V and B tiles
-            for (int it = 0; it < nk; it++) {
+            // producer: TMA loads of V (R row tiles) and B, KC chunks per stage
+            for (int it = 0; it < nst; it++) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u) || *s_fail) {
                     *s_fail = 1;
                     break;
                 }
-                mbar_expect_tx(&full[s], A_STAGE_BYTES + NB * BK * 2);
-                const int x = (kb0 + it) * BK;
-                tma_load_2d(sA + s * A_STAGE_BYTES, &tmA, &full[s], x, blockIdx.x * BM);
-                tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], x, 0);
+                mbar_expect_tx(&full[s], (uint32_t)nt * KC * A_BOX_BYTES + KC * NB * BK * 2);
+#pragma unroll
+                for (int c = 0; c < KC; c++) {
+                    const int x = (kb0 + it * KC + c) * BK;
+#pragma unroll
+                    for (int t = 0; t < R; t++)
+                        if (t < nt)
+                            tma_load_2d(sA + s * SM::A_STAGE + (t * KC + c) * A_BOX_BYTES, &tmA, &full[s], x,
+                                        (tile0 + t) * BM);
+                    tma_load_2d(sB + s * SM::B_STAGE + c * SM::B_BOX, &tmB, &full[s], x, 0);
+                }
                 issued = it + 1;
             }
         } else if (warp == 1 && lane == 0) {
-            // MMA issuer
+            // MMA issuer: R accumulators, NB columns apart in TMEM
             constexpr uint32_t idesc = umma_idesc_bf16(NB);
-            for (int it = 0; it < nk; it++) {
+            for (int it = 0; it < nst; it++) {
                 const int s = it % STAGES;
                 const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                 if (!mbar_wait(&full[s], ph) || *s_fail) {
@@ -200,13 +226,21 @@ k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(sA + s * A_STAGE_BYTES);
-                const uint32_t b0 = smem_u32(sB + s * B_STAGE);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; kk++) {
-                    const uint64_t da = umma_desc_sw128(a0 + kk * 32);
-                    const uint64_t db = umma_desc_sw128(b0 + kk * 32);
-                    umma_bf16(tmem_d, da, db, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                for (int c = 0; c < KC; c++) {
+                    const uint32_t b0 = smem_u32(sB + s * SM::B_STAGE + c * SM::B_BOX);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++) {
+                        const uint64_t db = umma_desc_sw128(b0 + kk * 32);
+#pragma unroll
+                        for (int t = 0; t < R; t++) {
+                            if (t >= nt) continue;
+                            const uint32_t a0 = smem_u32(sA + s * SM::A_STAGE + (t * KC + c) * A_BOX_BYTES);
+                            const uint64_t da = umma_desc_sw128(a0 + kk * 32);
+                            umma_bf16(tmem_d + (uint32_t)(t * NB), da, db, idesc,
+                                      (it > 0 || c > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
                 }
                 umma_commit(&empty[s]);
             }
@@ -229,22 +263,26 @@ k_tc_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
     } else {
-        // epilogue: warp w owns TMEM lanes [32w, 32w + 32) = rows of this tile
-        const int row = blockIdx.x * BM + warp * 32 + lane;
-        float* out = part + ((size_t)blockIdx.y * rows_valid + row) * NB;
+        // epilogue: warp w owns TMEM lanes [32w, 32w + 32) = rows of each tile
 #pragma unroll
-        for (int c0 = 0; c0 < NB; c0 += 16) {
-            float v[16];
-            if (nk > 0) {
-                tmem_ld16<NB>(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            } else {
+        for (int t = 0; t < R; t++) {
+            if (t >= nt) continue;
+            const int row = (tile0 + t) * BM + warp * 32 + lane;
+            float* out = part + ((size_t)blockIdx.y * rows_valid + row) * NB;
 #pragma unroll
-                for (int k = 0; k < 16; k++) v[k] = 0.f;
-            }
-            if (row < rows_valid) {
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+                float v[16];
+                if (nst > 0) {
+                    tmem_ld16<NB>(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NB + c0), v);
+                } else {
 #pragma unroll
-                for (int k = 0; k < 16; k += 4)
-                    *reinterpret_cast<float4*>(out + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    for (int k = 0; k < 16; k++) v[k] = 0.f;
+                }
+                if (row < rows_valid) {
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4)
+                        *reinterpret_cast<float4*>(out + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                }
             }
         }
     }
@@ -320,30 +358,77 @@ CUtensorMap make_map(const void* base, uint64_t k_elems, uint64_t rows, uint32_t
     return m;
 }
 
-template <int NB>
-void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int rows, long kelems, float* part,
-               size_t part_elems, int* err, int* nsplit_out, cudaStream_t st) {
+template <int NB, int R, int KC>
+void launch_tc_shape(const CUtensorMap& ma, const CUtensorMap& mb, int rows, long kelems, float* part,
+                     size_t part_elems, int* err, int* nsplit_out, cudaStream_t st) {
+    using SM = TcSmem<NB, R, KC>;
     const int nkb = (int)((kelems + BK - 1) / BK);
     const int tiles = (rows + BM - 1) / BM;
-    // ~2 CTAs per SM on 152 SMs; every CTA keeps >= 16 K-blocks of work
-    int want = (304 + tiles - 1) / tiles;
-    int maxs = nkb / 16 > 0 ? nkb / 16 : 1;
-    int nsplit = want < maxs ? want : maxs;
+    const int groups = (tiles + R - 1) / R;
+    static int occ = 0, nsm = 0;
+    if (!occ) {
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_proj<NB, R, KC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::BYTES));
+        int dev = 0;
+        SEEDCG_CUDA_TRY(cudaGetDevice(&dev));
+        SEEDCG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        SEEDCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tc_proj<NB, R, KC>, 128,
+                                                                      SM::BYTES));
+        if (occ < 1) throw Error{SEEDCG_ERR_CUDA, "tensor-core projection does not fit on an SM"};
+    }
+    // whole waves (two by default; SEEDCG_TC_WAVES overrides): as many K splits
+    // as keep groups * nsplit within waves x the resident CTAs, each split at
+    // least 16 chunks long and a multiple of KC chunks
+    int waves = 2;
+    if (const char* e = getenv("SEEDCG_TC_WAVES")) waves = std::max(1, std::min(8, atoi(e)));
+    const int resident = nsm * occ * waves;
+    int nsplit = resident / groups;
+    if (nsplit < 1) nsplit = 1;
+    const int maxs = nkb / 16 > 0 ? nkb / 16 : 1;
+    if (nsplit > maxs) nsplit = maxs;
     long cap = (long)(part_elems / ((size_t)rows * NB));
     if (nsplit > cap) nsplit = (int)cap;
     if (nsplit < 1) throw Error{SEEDCG_ERR_OOM, "tensor-core projection: partial buffer too small"};
     int per = (nkb + nsplit - 1) / nsplit;
+    per = (per + KC - 1) / KC * KC;
     nsplit = (nkb + per - 1) / per;
-    const uint32_t smem = TcSmem<NB>::BYTES;
-    static bool attr_set = false;
-    if (!attr_set) {
-        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_tc_proj<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
-    dim3 grid(tiles, nsplit);
-    k_tc_proj<NB><<<grid, 128, smem, st>>>(ma, mb, nkb, per, rows, part, err);
+    dim3 grid(groups, nsplit);
+    k_tc_proj<NB, R, KC><<<grid, 128, SM::BYTES, st>>>(ma, mb, nkb, per, rows, part, err);
     SEEDCG_CHECK_LAUNCH();
     *nsplit_out = nsplit;
+}
+
+// row tiles per CTA (R) and K chunks per stage (KC); SEEDCG_TC_SHAPE="R,KC"
+// overrides the default for measurements
+void tc_shape(int& r, int& kc) {
+    r = 4;
+    kc = 1;
+    if (const char* e = getenv("SEEDCG_TC_SHAPE")) {
+        int a = 0, b = 0;
+        if (sscanf(e, "%d,%d", &a, &b) == 2 && (a == 1 || a == 2 || a == 4) && (b == 1 || b == 2 || b == 4)) {
+            r = a;
+            kc = b;
+        }
+    }
+}
+
+template <int NB>
+void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int rows, long kelems, float* part,
+               size_t part_elems, int* err, int* nsplit_out, cudaStream_t st) {
+    int r, kc;
+    tc_shape(r, kc);
+#define SEEDCG_TC(RR, KK)                                                                             \
+    if (r == RR && kc == KK) {                                                                        \
+        launch_tc_shape<NB, RR, KK>(ma, mb, rows, kelems, part, part_elems, err, nsplit_out, st);   \
+        return;                                                                                       \
+    }
+    SEEDCG_TC(1, 1)
+    SEEDCG_TC(2, 1)
+    SEEDCG_TC(2, 2)
+    SEEDCG_TC(1, 2)
+    SEEDCG_TC(1, 4)
+#undef SEEDCG_TC
+    launch_tc_shape<NB, 4, 1>(ma, mb, rows, kelems, part, part_elems, err, nsplit_out, st);
 }
 
 }  // namespace

@@ -96,15 +96,19 @@ def test_tiny_fp64_full_solve_matches_oracle(seed_mode):
     s.close()
 
 
-@pytest.mark.parametrize("precision", ["mixed_v32", "mixed_vbf16"])
-def test_tiny_mixed_meets_residual_bar(precision):
+@pytest.mark.parametrize("precision,tc", [("mixed_v32", 1), ("mixed_vbf16", 1), ("mixed_vbf16", 0),
+                                          ("mixed_vbf16", 2)])
+def test_tiny_mixed_meets_residual_bar(precision, tc):
+    """tc: use_tensor_cores (bf16 basis: 1 tcgen05 for the seeds only, 2 also for
+    the PO projection, 0 never)."""
     need_gpu()
     dims, u, kappa, op, eta, B, wl = _tiny()
     Md = op.dense(WilsonOperator.OP_M)
     ev = np.linalg.eigvalsh(Md)
     cond = ev[-1] / ev[0]
     Xd = np.linalg.solve(Md, B.T).T
-    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, precision=precision)
+    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, precision=precision,
+                      use_tensor_cores=tc)
     Bd = _gpu_B(s, eta)
     X = dev(np.zeros_like(eta))
     code, info = s.solve(Bd, X, TOL, 0, wl.reorth_period)

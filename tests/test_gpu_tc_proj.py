@@ -42,3 +42,32 @@ def test_tc_projection_matches_fp64(dims, nvec, rows):
     # and the bf16 rounding of x is really all that separates the two paths
     assert np.abs(c_tc - exact).max() > 0
     s.close()
+
+
+@pytest.mark.parametrize("shape", ["1,1", "2,1", "4,1", "2,2", "1,2", "1,4"])
+def test_tc_projection_every_tile_shape(shape, monkeypatch):
+    """Every (row tiles per CTA, K chunks per stage) shape of the tensor-core
+    projection gives the FP64 product within the bf16 bound, including CTAs
+    whose last row tiles are past the valid rows."""
+    need_gpu()
+    dims, nvec, rows = (8, 8, 8, 8), 3, 300
+    u = W.gauge_field(dims, 0.5, 3)
+    s = seedcg.Solver(dims, u, 0.19, precision="mixed_vbf16", stop_after_seed=1,
+                      past_factor=1.0, m_max=rows)
+    eta = W.z2_sources(dims, 1, 3)
+    X = dev(np.zeros_like(eta))
+    s.solve(dev(eta), X, 1e-14, 0, 10, allow_not_converged=True)
+    m = seedcg.seedcg_get_lanczos(s.h, 1)[3]
+    assert m >= 129
+    rows = min(rows, m)
+    V = dev(np.zeros((rows,) + eta.shape[1:], dtype=np.complex128))
+    seedcg.seedcg_get_basis(s.h, 0, rows, V)
+    Vh = host(V).reshape(rows, -1)
+    xs = W.random_spinors(dims, nvec, 12)
+    exact = Vh.conj() @ xs.reshape(nvec, -1).T
+    scale = np.linalg.norm(Vh, axis=1)[:, None] * np.linalg.norm(xs.reshape(nvec, -1), axis=1)[None, :]
+    monkeypatch.setenv("SEEDCG_TC_SHAPE", shape)
+    for r in (rows, 129, 1):   # several tile counts, the last CTA partly or wholly past them
+        c_tc = seedcg.seedcg_project_basis(s.h, r, nvec, dev(xs), use_tensor_cores=1)
+        assert np.all(np.abs(c_tc - exact[:r]) <= (2.0 ** -9 + 2e-6) * scale[:r]), (shape, r)
+    s.close()
