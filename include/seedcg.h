@@ -84,6 +84,13 @@ typedef struct {
     int use_guess;         /* 1: start every system from the learned guess x_0 = net(b)
                               (weights set by seedcg_guess_set_weights/_train); a system
                               whose guess has ||b - M x_0|| >= ||b|| starts from 0 */
+    int resid_mode;        /* 0 (default): B holds b of M x = b, and ||b - M x|| <= tol ||b||
+                              (FP64) is the stopping criterion.  1: B holds eta of the
+                              original system D x = eta (Section 3 monitors its residual);
+                              the solve forms b = D^dag eta, and ||eta - D x|| <= tol ||eta||,
+                              recomputed in FP64, is the binding criterion: systems that miss
+                              it continue CG with a tighter M tolerance (up to six rounds).
+                              seedcg_solve only. */
 } seedcg_options;
 
 typedef struct {
@@ -98,6 +105,8 @@ typedef struct {
     int* matvecs;          /* per RHS: applications of D or D^dag                        */
     double* true_resid;    /* per RHS: ||b - M x|| / ||b||, FP64                         */
     float ms_total, ms_lanczos, ms_po, ms_seed, ms_cg;   /* device-event phase times    */
+    double* true_resid_D;  /* per RHS: ||eta - D x|| / ||eta||, FP64; written only when
+                              resid_mode = 1 (NULL to skip)                               */
 } seedcg_info;
 
 /* Fill *opt with the defaults documented above. */

@@ -48,6 +48,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
     if (o.use_tensor_cores < 0 || o.use_tensor_cores > 2) { why = "use_tensor_cores must be 0, 1 or 2"; return false; }
     if (o.use_guess < 0 || o.use_guess > 1) { why = "use_guess must be 0 or 1"; return false; }
+    if (o.resid_mode < 0 || o.resid_mode > 1) { why = "resid_mode must be 0 or 1"; return false; }
     return true;
 }
 
@@ -70,6 +71,7 @@ void seedcg_default_options(seedcg_options* opt) {
     opt->poll_every = 32;
     opt->use_tensor_cores = 1;
     opt->use_guess = 0;
+    opt->resid_mode = 0;
 }
 
 seedcg_status seedcg_create(seedcg_handle** out, const int dims[4], const double* gauge,
@@ -192,6 +194,8 @@ seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrh
         if (nrhs[f] < 1 || nrhs[f] > 256) return fail(h0, SEEDCG_ERR_ARG, "batch: nrhs must be in [1, 256]");
         if (hs[f]->opt.precision != h0->opt.precision || hs[f]->device != h0->device)
             return fail(h0, SEEDCG_ERR_ARG, "batch: all handles need the same precision and device");
+        if (hs[f]->opt.resid_mode != 0)
+            return fail(h0, SEEDCG_ERR_ARG, "batch: resid_mode = 1 is supported by seedcg_solve only");
         for (int g = 0; g < f; g++)
             if (hs[g] == hs[f]) return fail(h0, SEEDCG_ERR_ARG, "batch: a handle appears twice");
         total += nrhs[f];

@@ -138,7 +138,7 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
     const cx_t<R>* in = DAG ? gd.t : gd.p;
     cx_t<R>* out = DAG ? gd.q : gd.t;
     for (int r = qg; r < nsys; r += RPB) {
-        double d = 0.0;
+        R dr = 0;
         if (live) {
             const cx_t<R>* inr = in + (size_t)r * gd.n;
             Spinor<R> res;
@@ -154,11 +154,12 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
                     const cx_t<R> rz = res.c[k / 3][k % 3];
                     acc += pz.x * rz.x + pz.y * rz.y;
                 }
-                d = (double)acc;
+                dr = acc;
             }
         }
         if (DOT) {
-            d = warp_sum(d);
+            // lanes in the working precision, tiles in FP64 (k_mf_alpha)
+            const double d = (double)warp_sum_t(dr);
             if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
         }
     }

@@ -10,18 +10,13 @@
 
 #include "internal.cuh"
 #include "wilson.cuh"
+#include "reduce.cuh"
 
 namespace seedcg {
 
 namespace {
 
 constexpr int kThreads = 128;
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
 
 inline int blocks_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
 
@@ -180,8 +175,10 @@ struct Brick {
     int ny, nz;             // bricks along y and z
 };
 
-template <typename R, int DAG, int TB, bool DOT = false>
-__global__ void __launch_bounds__(384, (sizeof(R) == 4 ? 2 : 1))
+// PIPE: at most 256 threads and up to 128 registers per thread, spent on
+// keeping more neighbour spinors in flight (wilson_site_prescaled_pipe)
+template <typename R, int DAG, int TB, bool DOT = false, bool PIPE = false>
+__global__ void __launch_bounds__(PIPE ? 256 : 384, (sizeof(R) == 4 ? 2 : 1))
 k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
                const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out,
                const cx_t<R>* __restrict__ pdot = nullptr, double* __restrict__ part = nullptr) {
@@ -230,7 +227,10 @@ k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
             cx_t<R>* outr = out + (size_t)r * 12 * vol;
             Spinor<R> res;
             auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
-            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            if constexpr (PIPE)
+                wilson_site_prescaled_pipe<DAG, R>(nb, s, load, fl, bl, res);
+            else
+                wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
             store_spinor(outr, vol, s, res);
         }
         return;
@@ -238,13 +238,16 @@ k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
     const int passes = (n + rpb - 1) / rpb;
     for (int pass = 0; pass < passes; pass++) {
         const int r = pass * rpb + q;
-        double d = 0.0;
+        R dr = 0;
         if (r < n) {
             const cx_t<R>* inr = in + (size_t)r * 12 * vol;
             cx_t<R>* outr = out + (size_t)r * 12 * vol;
             Spinor<R> res;
             auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
-            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            if constexpr (PIPE)
+                wilson_site_prescaled_pipe<DAG, R>(nb, s, load, fl, bl, res);
+            else
+                wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
             store_spinor(outr, vol, s, res);
             if (DOT) {
                 // Re p^dag (this result) at this site, for the CG step length
@@ -256,12 +259,13 @@ k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
                     const cx_t<R> rz = res.c[k / 3][k % 3];
                     acc += pz.x * rz.x + pz.y * rz.y;
                 }
-                d = (double)acc;
+                dr = acc;
             }
         }
         if (DOT) {
-            // TB threads (TB/32 whole warps) share r: warp sums, then a fixed-order sum
-            d = warp_sum_d(d);
+            // TB threads (TB/32 whole warps) share r: warp sums in the working
+            // precision, then a fixed-order FP64 sum over the warps
+            const double d = (double)warp_sum_t(dr);
             __syncthreads();
             if ((threadIdx.x & 31) == 0) sdot_w[threadIdx.x >> 5] = d;
             __syncthreads();
@@ -294,17 +298,18 @@ bool make_brick(const Geom& g, Brick& br, int cap = 128) {
 
 // one launch of a brick kernel; the dynamic shared memory limit is raised once
 // per instantiation (each has its own static flag)
-template <typename R, int DAG, int TB, bool DOT>
+template <typename R, int DAG, int TB, bool DOT, bool PIPE = false>
 void brick_go(int nb, int threads, size_t smem, cudaStream_t st, const Geom& g, const Brick& br,
               const cx_t<R>* u, R kappa, int n, const cx_t<R>* in, cx_t<R>* out,
               const cx_t<R>* pdot, double* part) {
     static bool attr = false;
     if (!attr) {
-        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_dslash_brick<R, DAG, TB, DOT>,
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_dslash_brick<R, DAG, TB, DOT, PIPE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         attr = true;
     }
-    k_dslash_brick<R, DAG, TB, DOT><<<nb, threads, smem, st>>>(g, br, u, kappa, n, in, out, pdot, part);
+    k_dslash_brick<R, DAG, TB, DOT, PIPE><<<nb, threads, smem, st>>>(g, br, u, kappa, n, in, out, pdot,
+                                                                     part);
     SEEDCG_CHECK_LAUNCH();
 }
 
@@ -327,7 +332,8 @@ void launch_dslash(const Geom& g, const cx_t<R>* u, R kappa, int dag, const cx_t
 // ---------------------------------------------------------------------------
 struct BrickChoice {
     int cap;
-    int rpb;   // 0 = balanced default
+    int rpb;    // 0 = balanced default
+    int pipe;   // 1 = the register-pipelined site kernel (<= 256 threads)
 };
 
 template <typename R>
@@ -352,9 +358,9 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
             FILE* f = fopen(path, "r");
             if (f) {
                 char k[512];
-                int a, b;
-                while (fscanf(f, "%511s %d %d", k, &a, &b) == 3)
-                    if (std::string(k) == key) cache[key] = BrickChoice{a, b};
+                int a, b, c;
+                while (fscanf(f, "%511s %d %d %d", k, &a, &b, &c) == 4)
+                    if (std::string(k) == key) cache[key] = BrickChoice{a, b, c};
                 fclose(f);
                 it = cache.find(key);
                 if (it != cache.end()) return it->second;
@@ -363,8 +369,10 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
     }
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap_status);
-    if (cap_status != cudaStreamCaptureStatusNone) return BrickChoice{128, 0};  // no timing inside a capture
-    const BrickChoice cands[] = {{128, 0}, {128, 2}, {128, 1}, {64, 0}, {64, 4}, {64, 3}};
+    if (cap_status != cudaStreamCaptureStatusNone) return BrickChoice{128, 0, 0};  // no timing inside a capture
+    const BrickChoice cands[] = {{128, 0, 0}, {128, 2, 0}, {128, 1, 0}, {64, 0, 0}, {64, 4, 0},
+                                 {64, 3, 0},  {128, 2, 1}, {128, 1, 1}, {64, 4, 1}, {64, 2, 1}};
+    const bool tune_log = getenv("SEEDCG_TUNE_LOG") != nullptr;
     cudaEvent_t a, b;
     SEEDCG_CUDA_TRY(cudaEventCreate(&a));
     SEEDCG_CUDA_TRY(cudaEventCreate(&b));
@@ -381,6 +389,9 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
         SEEDCG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (tune_log)
+            fprintf(stderr, "seedcg tune %s: cap %d rpb %d pipe %d: %.4f ms\n", key, c.cap, c.rpb, c.pipe,
+                    ms / 3);
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
@@ -393,7 +404,7 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
     if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
         FILE* f = fopen(path, "a");
         if (f) {
-            fprintf(f, "%s %d %d\n", key, best.cap, best.rpb);
+            fprintf(f, "%s %d %d %d\n", key, best.cap, best.rpb, best.pipe);
             fclose(f);
         }
     }
@@ -407,11 +418,11 @@ void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
                         const BrickChoice* force) {
     if (n <= 0) return;
     Brick br;
-    BrickChoice ch{128, 0};
+    BrickChoice ch{128, 0, 0};
     if (force) ch = *force;
     else if (!pdot) ch = tuned_brick<R>(g, u, kappa, dag, n, in, out, st);
     if (make_brick(g, br, ch.cap) && (br.tb == 64 || br.tb == 96 || br.tb == 128)) {
-        const int maxr = 384 / br.tb;
+        const int maxr = (ch.pipe ? 256 : 384) / br.tb;
         const int passes = (n + maxr - 1) / maxr;
         const int rpb = ch.rpb > 0 ? std::min(ch.rpb, maxr) : (n + passes - 1) / passes;
         const int threads = br.tb * rpb;
@@ -425,7 +436,13 @@ void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
             if (nblocks_out) *nblocks_out = nb;
             return;
         }
-        if (br.tb == 128) {
+        if (ch.pipe && br.tb == 128) {
+            if (dag) brick_go<R, 1, 128, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 0, 128, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+        } else if (ch.pipe && br.tb == 64) {
+            if (dag) brick_go<R, 1, 64, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            else brick_go<R, 0, 64, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+        } else if (br.tb == 128) {
             if (dag) brick_go<R, 1, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
             else brick_go<R, 0, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
         } else if (br.tb == 96) {

@@ -13,6 +13,13 @@ namespace seedcg {
 constexpr int kRedThreads = 256;  // every reducing kernel uses this block size
 constexpr int kMaxRedBlocks = 4096;
 
+// warp sum in the value's own precision (FP32 sums stay off the scarce FP64 pipe)
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -1021,16 +1021,119 @@ seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const dou
     return SEEDCG_OK;
 }
 
+namespace {
+
+// ratio[j] = ||eta_j - D x_j|| / ||eta_j|| in FP64 (T: scratch of nrhs fields)
+void d_residuals(seedcg_handle* h, int nrhs, const double2* E64, const double2* X64, double2* T64,
+                 std::vector<double>& ratio, cudaStream_t st) {
+    const long n = 12L * h->g.vol;
+    dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, nrhs, X64, T64, st);
+    DevBuf nr;
+    nr.ensure(sizeof(double) * (4096 + 2 * nrhs) + sizeof(unsigned) * 64);
+    double* part = nr.as<double>();
+    double* norms = part + 4096;
+    unsigned* ctr = reinterpret_cast<unsigned*>(norms + 2 * nrhs);
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 64, st));
+    for (int j = 0; j < nrhs; j++) {
+        axpby_f64(E64 + (size_t)j * n, T64 + (size_t)j * n, n, st);  // T = eta - D x
+        k_norm2_public(E64 + (size_t)j * n, n, part, ctr, norms + j, st);
+        k_norm2_public(T64 + (size_t)j * n, n, part, ctr, norms + nrhs + j, st);
+    }
+    std::vector<double> hn(2 * nrhs);
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    ratio.assign(nrhs, 0.0);
+    for (int j = 0; j < nrhs; j++) ratio[j] = hn[j] > 0.0 ? hn[nrhs + j] / hn[j] : 0.0;
+}
+
+// Original-system criterion (resid_mode 1): while some ||eta - D x|| / ||eta|| > tol,
+// continue CG on those systems with an M tolerance tightened by the observed gap.
+seedcg_status d_residual_rounds(seedcg_handle* h, int nrhs, const double2* E64, const double2* B64,
+                                double2* X64, double2* T64, double tol, bool run_cg,
+                                seedcg_status code, seedcg_info* info, cudaStream_t st) {
+    const long n = 12L * h->g.vol;
+    const seedcg_options& o = h->opt;
+    std::vector<double> ratio;
+    d_residuals(h, nrhs, E64, X64, T64, ratio, st);
+    double tol_m = tol;
+    for (int round = 0; run_cg && code == SEEDCG_OK && round < 6; round++) {
+        std::vector<int> fail;
+        double worst = 0.0;
+        for (int j = 0; j < nrhs; j++)
+            if (!(ratio[j] <= tol)) {
+                fail.push_back(j);
+                worst = std::max(worst, ratio[j]);
+            }
+        if (fail.empty() || !std::isfinite(worst)) break;
+        tol_m *= std::max(0.01, 0.5 * tol / worst);
+        const int nf = (int)fail.size();
+        DevBuf gb, gx;
+        gb.ensure((size_t)nf * n * sizeof(double2));
+        gx.ensure((size_t)nf * n * sizeof(double2));
+        for (int k = 0; k < nf; k++) {
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(gb.as<double2>() + (size_t)k * n, B64 + (size_t)fail[k] * n,
+                                            n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(gx.as<double2>() + (size_t)k * n, X64 + (size_t)fail[k] * n,
+                                            n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        }
+        std::vector<CgGroup> gs{{h, nf, gb.as<double2>(), gx.as<double2>()}};
+        CgResult cgr;
+        if (o.precision == SEEDCG_FP64)
+            batched_cg<double>(gs, tol_m, 0.0, o.cg_maxiter, o.poll_every, true, h->cgbuf, h->pinned, cgr, st);
+        else
+            batched_cg<float>(gs, tol_m, o.reliable_delta, o.cg_maxiter, o.poll_every, true, h->cgbuf,
+                              h->pinned, cgr, st);
+        for (int k = 0; k < nf; k++)
+            SEEDCG_CUDA_TRY(cudaMemcpyAsync(X64 + (size_t)fail[k] * n, gx.as<double2>() + (size_t)k * n,
+                                            n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        bool stuck = false;
+        if (info) {
+            info->reliable_updates += cgr.reliable_updates;
+            for (int k = 0; k < nf; k++) {
+                const int j = fail[k];
+                if (info->iters) info->iters[j] += cgr.iters[0][k];
+                if (info->matvecs) info->matvecs[j] += 2 * (cgr.iters[0][k] + cgr.ru[0][k]) + 2;
+                if (info->true_resid) info->true_resid[j] = cgr.true_resid[0][k];
+            }
+        }
+        for (int k = 0; k < nf; k++) stuck = stuck || cgr.notconv[0][k];
+        d_residuals(h, nrhs, E64, X64, T64, ratio, st);
+        if (stuck) break;
+    }
+    if (info) {
+        int mx = info->cg_iters_max;
+        if (info->iters)
+            for (int j = 1; j < nrhs; j++) mx = std::max(mx, info->iters[j]);
+        info->cg_iters_max = mx;
+        if (info->true_resid_D)
+            for (int j = 0; j < nrhs; j++) info->true_resid_D[j] = ratio[j];
+    }
+    if (run_cg && code == SEEDCG_OK)
+        for (int j = 0; j < nrhs; j++)
+            if (!(ratio[j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
+    return code;
+}
+
+}  // namespace
+
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
                          int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {
     // B, X: device canonical complex128 (the API layer stages host pointers)
     const int vol = h->g.vol;
     const long n = 12L * vol;
     const size_t fb = (size_t)nrhs * n * sizeof(double2);
-    h->staging.ensure(2 * fb + 512);
+    const bool dmode = h->opt.resid_mode == 1;
+    h->staging.ensure((dmode ? 4 : 2) * fb + 512);
     double2* B64 = h->staging.as<double2>();
     double2* X64 = B64 + (size_t)nrhs * n;
-    to_internal_f64(B, B64, vol, nrhs, st);
+    double2* E64 = dmode ? X64 + (size_t)nrhs * n : nullptr;   // eta of D x = eta
+    double2* T64 = dmode ? E64 + (size_t)nrhs * n : nullptr;   // scratch
+    if (dmode) {
+        to_internal_f64(B, E64, vol, nrhs, st);
+        dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, nrhs, E64, B64, st);  // b = D^dag eta
+    } else {
+        to_internal_f64(B, B64, vol, nrhs, st);
+    }
     if (h->opt.x0_given)
         to_internal_f64(X, X64, vol, nrhs, st);
     else
@@ -1073,6 +1176,8 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
             code = run_solve<float, __nv_bfloat162>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
             break;
     }
+    if (dmode)
+        code = d_residual_rounds(h, nrhs, E64, B64, X64, T64, tol, !h->opt.stop_after_seed, code, info, st);
     from_internal_f64(X64, X, vol, nrhs, st);
     SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
     return code;

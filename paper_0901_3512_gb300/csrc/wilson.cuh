@@ -209,4 +209,35 @@ __device__ __forceinline__ void wilson_site_prescaled(const Nbr& n, int s, LoadN
 #undef SEEDCG_HOP
 }
 
+// Same result as wilson_site_prescaled, written for a looser register budget:
+// the forward and backward neighbours of each direction are loaded together and
+// the next direction's pair is requested before the current one is consumed,
+// so two to four spinors are in flight per thread instead of one.
+template <int DAG, typename R, typename LoadNbr, typename Fwd, typename Bwd>
+__device__ __forceinline__ void wilson_site_prescaled_pipe(const Nbr& n, int s, LoadNbr load, Fwd fl,
+                                                           Bwd bl, Spinor<R>& out) {
+    constexpr int SF = DAG ? 1 : -1;
+    constexpr int SB = -SF;
+    Spinor<R> pf, pb, qf, qb;
+    load(n.f[0], pf);
+    load(n.b[0], pb);
+    load(s, out);
+#define SEEDCG_HOP2(MU, CF, CB, NF, NB, NEXT)                                                   \
+    {                                                                                           \
+        auto lf = [&](int a, int b) { return fl(MU, 3 * a + b); };                              \
+        auto lb = [&](int a, int b) { return bl(MU, 3 * a + b); };                              \
+        if (NEXT) {                                                                             \
+            load(n.f[(MU + 1) & 3], NF);                                                        \
+            load(n.b[(MU + 1) & 3], NB);                                                        \
+        }                                                                                       \
+        hop<MU, SF, false, R, decltype(lf), false>(out, CF, lf, R(1));                          \
+        hop<MU, SB, true, R, decltype(lb), false>(out, CB, lb, R(1));                           \
+    }
+    SEEDCG_HOP2(0, pf, pb, qf, qb, true)
+    SEEDCG_HOP2(1, qf, qb, pf, pb, true)
+    SEEDCG_HOP2(2, pf, pb, qf, qb, true)
+    SEEDCG_HOP2(3, qf, qb, pf, pb, false)
+#undef SEEDCG_HOP2
+}
+
 }  // namespace seedcg

@@ -39,7 +39,8 @@ class seedcg_options(ctypes.Structure):
                 ("po_passes", ctypes.c_int), ("seed_mode", ctypes.c_int),
                 ("x0_given", ctypes.c_int), ("cg_maxiter", ctypes.c_int),
                 ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int),
-                ("use_tensor_cores", ctypes.c_int), ("use_guess", ctypes.c_int)]
+                ("use_tensor_cores", ctypes.c_int), ("use_guess", ctypes.c_int),
+                ("resid_mode", ctypes.c_int)]
 
 
 class seedcg_info(ctypes.Structure):
@@ -49,7 +50,8 @@ class seedcg_info(ctypes.Structure):
                 ("matvecs", ctypes.POINTER(ctypes.c_int)),
                 ("true_resid", ctypes.POINTER(ctypes.c_double)),
                 ("ms_total", ctypes.c_float), ("ms_lanczos", ctypes.c_float),
-                ("ms_po", ctypes.c_float), ("ms_seed", ctypes.c_float), ("ms_cg", ctypes.c_float)]
+                ("ms_po", ctypes.c_float), ("ms_seed", ctypes.c_float), ("ms_cg", ctypes.c_float),
+                ("true_resid_D", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -190,9 +192,11 @@ def seedcg_solve(h, nrhs: int, B, X, tol: float, extra_iters: int, reorth_period
     iters = (ctypes.c_int * nrhs)()
     mv = (ctypes.c_int * nrhs)()
     tr = (ctypes.c_double * nrhs)()
+    trd = (ctypes.c_double * nrhs)(*([float("nan")] * nrhs))
     info.iters = iters
     info.matvecs = mv
     info.true_resid = tr
+    info.true_resid_D = trd
     code = load().seedcg_solve(h, int(nrhs), ctypes.c_void_p(_ptr(B)), ctypes.c_void_p(_ptr(X)),
                                float(tol), int(extra_iters), int(reorth_period),
                                ctypes.byref(info), _stream_ptr(stream))
@@ -200,6 +204,7 @@ def seedcg_solve(h, nrhs: int, B, X, tol: float, extra_iters: int, reorth_period
     out = {"status": code, "m_conv": info.m_conv, "m": info.m, "po_count": info.po_count,
            "cg_iters_max": info.cg_iters_max, "reliable_updates": info.reliable_updates,
            "iters": list(iters), "matvecs": list(mv), "true_resid": list(tr),
+           "true_resid_D": list(trd),
            "ms_total": info.ms_total, "ms_lanczos": info.ms_lanczos, "ms_po": info.ms_po,
            "ms_seed": info.ms_seed, "ms_cg": info.ms_cg}
     return code, out

@@ -33,6 +33,7 @@ def test_default_options_are_host_only():
     o = seedcg.seedcg_default_options()
     assert o.m_max == 4000 and o.past_factor == 1.0 and o.precision == seedcg.SEEDCG_FP64
     assert o.reliable_delta == pytest.approx(0.1) and o.po_passes == 1 and o.seed_mode == 1
+    assert o.use_tensor_cores == 1 and o.use_guess == 0 and o.resid_mode == 0
 
 
 @pytest.mark.parametrize("dims", [(3, 4, 4, 4), (4, 4, 4, 0), (4, 4, 4, 1)])
@@ -46,7 +47,8 @@ def test_create_rejects_bad_dims_before_device_work(dims):
 def test_create_rejects_bad_options():
     g = np.zeros(16 * 36, dtype=np.complex128)
     for kw in ({"past_factor": 0.5}, {"precision": 7}, {"po_passes": 3},
-               {"seed_mode": 0, "precision": "mixed_v32"}, {"m_max": 0}):
+               {"seed_mode": 0, "precision": "mixed_v32"}, {"m_max": 0}, {"resid_mode": 2},
+               {"use_tensor_cores": 3}):
         with pytest.raises(seedcg.SeedCGError) as e:
             seedcg.seedcg_create((2, 2, 2, 2), g, 0.1, seedcg.make_options(**kw))
         assert e.value.code == seedcg.SEEDCG_ERR_ARG

@@ -254,3 +254,29 @@ def test_po_guard_when_orthogonality_is_lost():
         tr = np.linalg.norm(B[j] - op.M(got[j])) / np.linalg.norm(B[j])
         assert info["true_resid"][j] <= TOL and tr <= TOL
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_v32"])
+def test_original_system_residual_is_binding(precision):
+    """resid_mode = 1: B holds eta of D x = eta; the residual Section 3 monitors,
+    ||eta - D x|| / ||eta||, recomputed here with the oracle's D, meets tol and
+    equals the reported true_resid_D; the solution is D^-1 eta within
+    cond(D) * tol."""
+    need_gpu()
+    dims, u, kappa, op, eta, B, wl = _tiny()
+    Dd = op.dense(WilsonOperator.OP_D)
+    sv = np.linalg.svd(Dd, compute_uv=False)
+    cond_d = sv[0] / sv[-1]
+    E = eta.reshape(len(eta), -1)
+    Xd = np.linalg.solve(Dd, E.T).T
+    s = seedcg.Solver(dims, u, kappa, past_factor=wl.past_factor, precision=precision, resid_mode=1)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(dev(eta), X, TOL, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        rd = np.linalg.norm(E[j] - op.D(got[j])) / np.linalg.norm(E[j])
+        assert rd <= TOL, (j, rd)
+        assert abs(info["true_resid_D"][j] - rd) <= 1e-3 * rd + 1e-15
+        assert rel(got[j], Xd[j]) <= cond_d * TOL
+    s.close()
