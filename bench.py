@@ -35,6 +35,10 @@ DEFAULT_WORKLOAD = "large_16x16x16x32_nrhs12"
 METRIC = "time-to-solution, all nrhs at rel. residual 1e-8 (s); dslash HBM GB/s vs peak"
 
 
+# measured DRAM read + write bytes / algorithmic bytes of the PO step (projection + subtraction)
+PO_DRAM_PER_ALG_BF16 = 1.01
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -336,8 +340,13 @@ def run_ours(args):
     po_alg_bytes = 2 * po_rows * n * vbytes  # V_{1:i-1} read by the projection and the update
     po_s = info["ms_po"] / 1000.0
     po_gbs = po_alg_bytes / po_s / 1e9 if po_s > 0 else None
+    # DRAM bytes per algorithmic byte of the PO kernels, from the 1-pass ncu window of this
+    # workload (profiles/po_kernels_bf16_16x16x16x32.md); only for the configuration measured
+    traffic = (round(PO_DRAM_PER_ALG_BF16 * po_alg_bytes)
+               if prec == "mixed_vbf16" and args.workload == "large_16x16x16x32_nrhs12" else None)
     roofline = {"bound": "hbm", "achieved": po_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": (po_gbs / peaks["hbm_gbs"]) if po_gbs else None, "traffic": None,
+                "frac": (po_gbs / peaks["hbm_gbs"]) if po_gbs else None, "traffic": traffic,
+                "traffic_unit": "bytes per solve",
                 "kernel": "periodic re-orthogonalisation (V^dag [v,f] projection + [v,f] -= V c)",
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_solve": po_alg_bytes, "ms_per_solve": info["ms_po"]}

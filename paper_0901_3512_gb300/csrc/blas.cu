@@ -152,7 +152,7 @@ k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__
 // V is read exactly once from HBM.
 // ---------------------------------------------------------------------------
 template <typename R, typename VT, int NV, int RPW, int CHUNK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && NV == 2) ? 4 : 1)
 k_proj_partial(const VT* __restrict__ V, long ldv, int na, const cx_t<R>* __restrict__ X,
                long ldx, int nv, long n, int chunk, int rg, double2* __restrict__ part) {
     // block (x, y): one chunk of entries (X chunk staged in shared memory)

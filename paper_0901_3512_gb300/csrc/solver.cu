@@ -623,8 +623,10 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     const size_t cols = (size_t)std::max(nrhs, 2);
     const size_t coef_elems = ms * cols;
     const bool seeds_streamed = !fp64 && !(std::is_same<VT, __nv_bfloat162>::value && o.use_tensor_cores);
+    // also room for three row segments of the PO subtraction (k_po_sub_seg partials)
+    const size_t seg3 = 3 * 2 * (size_t)n * sizeof(cx_t<R>) / sizeof(double2);
     const size_t split_elems = std::max<size_t>(
-        std::max<size_t>(coef_elems * 48, (size_t)1 << 20),
+        std::max<size_t>(std::max<size_t>(coef_elems * 48, (size_t)1 << 20), seg3),
         seeds_streamed ? proj_scratch_elems<R, VT>(n, m_max) : proj_scratch_elems<R, VT>(n, m_max) / 2);
     h->coef.ensure((coef_elems + split_elems) * sizeof(double2));
     double2* Cc = h->coef.as<double2>();
