@@ -58,6 +58,13 @@ def _args():
     p.add_argument("--tc-po", type=int, default=1, choices=[0, 1, 2],
                    help="with --only po: use_tensor_cores for the bf16 basis (0 SIMT, 1 default: "
                         "tcgen05 for the seeds only, 2 tcgen05 for the PO projection too)")
+    p.add_argument("--sweep", default=None, choices=["m", "k", "kappa"],
+                   help="Figs 1-2 / Table 1 of the paper on a synthetic field: CG matvecs of the "
+                        "second right-hand side against the past-convergence factor (m) or the PO "
+                        "period (k), first-RHS cost against k; 'kappa' scans --kappas. One JSON "
+                        "line per setting (not a bench line)")
+    p.add_argument("--kappa", type=float, default=None, help="with --sweep: kappa of the field")
+    p.add_argument("--kappas", default="", help="with --sweep kappa: comma-separated values")
     p.add_argument("--only", default=None, choices=["dslash", "po"],
                    help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
                         "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
@@ -473,8 +480,65 @@ def run_only(args):
     s.close()
 
 
+def run_sweep(args):
+    """The paper's parameter studies (Section 3, Figs 1-2, Table 1) on a synthetic field: two
+    point sources (spin 1, colours 1 and 2); the second system's CG matvecs after seeding
+    against standard CG from zero, as m (past factor) and k (PO period) vary."""
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[args.workload]
+    f = wl.fields[0]
+    prec = args.precision or "mixed_v32"
+    gauge = f.gauge()
+    eta_all = W.point_sources(f.dims, 2)
+
+    def run(kappa, pf, k, nrhs=2):
+        s = seedcg.Solver(f.dims, gauge, kappa, precision=prec, past_factor=pf, m_max=args.m_max)
+        eta = torch.from_numpy(eta_all[2 - nrhs:]).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        X = torch.zeros_like(B)
+        s.solve(B, X, wl.tol, 0, k, allow_not_converged=True)      # warm-up (autotuning)
+        X.zero_()
+        code, info = s.solve(B, X, wl.tol, 0, k, allow_not_converged=True)
+        s.close()
+        return code, info
+
+    def plain_cg(kappa):
+        # the second system alone, no past-convergence: D-Lanczos == CG from zero
+        code, info = run(kappa, 1.0, 0, nrhs=1)
+        return info["m_conv"] if info["m_conv"] else info["iters"][0]
+
+    if args.sweep == "kappa":
+        for kap in [float(x) for x in args.kappas.split(",") if x]:
+            cg0 = plain_cg(kap)
+            code, info = run(kap, 2.0, 10)
+            print(json.dumps({"sweep": "kappa", "kappa": kap, "plain_cg_iters_rhs2": cg0,
+                              "m_conv": info["m_conv"], "m": info["m"],
+                              "seeded_cg_iters_rhs2": info["iters"][1], "status": code}), flush=True)
+        return
+    kappa = args.kappa if args.kappa is not None else W.kappa_for(f.name)
+    cg0 = plain_cg(kappa)
+    base = {"workload": args.workload, "lattice": list(f.dims), "kappa": kappa, "precision": prec,
+            "tol": wl.tol, "plain_cg_iters_rhs2": cg0, "plain_cg_matvecs_rhs2": 2 * cg0}
+    settings = ([(pf, 10) for pf in (1.0, 1.2, 1.4, 1.6, 2.0)] if args.sweep == "m"
+                else [(1.4, k) for k in (10, 100, 200, 250, 0)])
+    for pf, k in settings:
+        code, info = run(kappa, pf, k)
+        print(json.dumps(dict(base, sweep=args.sweep, past_factor=pf, k=k, m_conv=info["m_conv"],
+                              m=info["m"], po_count=info["po_count"],
+                              cg_iters_rhs2=info["iters"][1], matvecs_rhs2=info["matvecs"][1],
+                              matvecs_rhs1=info["matvecs"][0],
+                              ms_rhs1=round(info["ms_lanczos"], 2), ms_po=round(info["ms_po"], 2),
+                              true_resid=[float(x) for x in info["true_resid"]], status=code)),
+              flush=True)
+
+
 def main():
     args = _args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.only:
         run_only(args)
         return
