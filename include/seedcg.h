@@ -158,7 +158,6 @@ seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrh
                                  void* stream);
 
 /*
- * Apply the operator to n spinor fields/*
  * Apply the operator to n spinor fields (for parity checks and for forming
  * b = D^dag eta).  op: 0 = D, 1 = D^dag, 2 = M = D^dag D.  prec: 0 = FP64
  * arithmetic, 1 = FP32 arithmetic (inputs rounded to FP32, result widened).
@@ -191,7 +190,6 @@ seedcg_status seedcg_apply_noalloc(seedcg_handle* h, int op, int prec, int multi
                                    const double* in, double* out, void* stream);
 
 /*
- * After a solve: copy the Lanczos scalars of RHS 1/*
  * After a solve: copy the Lanczos scalars of RHS 1 (alpha_1..m, beta_1..m,
  * delta_1..m; Eq. 2) into caller host arrays of `cap` doubles (any may be
  * NULL).  Returns the number m written via *m_out.
@@ -244,7 +242,6 @@ seedcg_status seedcg_guess_train(seedcg_handle* h, int npairs, const double* B, 
 seedcg_status seedcg_guess_predict(seedcg_handle* h, int n, const double* B, double* X0, void* stream);
 
 /*
- * Measurement helper: time `reps` launches/*
  * Measurement helper: time `reps` launches of the multi-RHS dslash D on n
  * internal spinor fields (prec 0 = FP64, 1 = FP32) with CUDA events on
  * `stream`, writing a 512 MB buffer between launches when flush_l2 != 0 so
