@@ -65,6 +65,14 @@ def _args():
                         "line per setting (not a bench line)")
     p.add_argument("--kappa", type=float, default=None, help="with --sweep: kappa of the field")
     p.add_argument("--kappas", default="", help="with --sweep kappa: comma-separated values")
+    p.add_argument("--guess-eval", action="store_true",
+                   help="learned initial guess on the workload's field: train on (b, x) pairs the "
+                        "solver produces, then solve held-out Z2 sources from x0 = 0 and from the "
+                        "learned x0 (iterations and time; one JSON line, not a bench line)")
+    p.add_argument("--train-pairs", type=int, default=2000)
+    p.add_argument("--eval-pairs", type=int, default=64)
+    p.add_argument("--epochs", type=int, default=10)
+    p.add_argument("--lr", type=float, default=3e-3)
     p.add_argument("--only", default=None, choices=["dslash", "po"],
                    help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
                         "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
@@ -534,8 +542,70 @@ def run_sweep(args):
               flush=True)
 
 
+def run_guess_eval(args):
+    """The learned initial guess at the workload's scale: training pairs (b = D^dag eta,
+    x = M^-1 b) from the solver on seeded Z2 sources, Adam training by the library's own
+    kernels, then held-out Z2 sources solved from x0 = 0 and from the learned x0."""
+    import numpy as np
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[args.workload]
+    f = wl.fields[0]
+    prec = args.precision or wl.precision
+    kappa = W.kappa_for(f.name)
+    chunk = 12
+    ntr = max(chunk, args.train_pairs // chunk * chunk)
+    nev = max(chunk, args.eval_pairs // chunk * chunk)
+    s = seedcg.Solver(f.dims, f.gauge(), kappa, precision=prec, past_factor=1.0, m_max=args.m_max)
+    vol = int(np.prod(f.dims))
+    Btr = torch.empty((ntr, vol, 4, 3), dtype=torch.complex128, device="cuda")
+    Xtr = torch.zeros_like(Btr)
+    t0 = time.time()
+    for c in range(ntr // chunk):
+        eta = torch.from_numpy(W.z2_sources(f.dims, chunk, f.seed, f.field_index, stream=100 + c)).cuda()
+        sl = slice(c * chunk, (c + 1) * chunk)
+        s.apply(seedcg.OP_DDAG, eta, Btr[sl], prec=0, multi=1)
+        code, _ = s.solve(Btr[sl], Xtr[sl], wl.tol, 0, wl.reorth_period)
+    torch.cuda.synchronize()
+    t_data = time.time() - t0
+    seedcg.seedcg_guess_set_weights(s.h, W.guess_weights(7))
+    t0 = time.time()
+    loss = seedcg.seedcg_guess_train(s.h, Btr, Xtr, args.epochs, 8, args.lr)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del Btr, Xtr
+    res = {"zero": {"iters": [], "ms": 0.0}, "guess": {"iters": [], "ms": 0.0}}
+    val_loss = []
+    for c in range(nev // chunk):
+        eta = torch.from_numpy(W.z2_sources(f.dims, chunk, f.seed, f.field_index, stream=500 + c)).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        for mode, use in (("zero", 0), ("guess", 1)):
+            s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max, use_guess=use)
+            X = torch.zeros_like(B)
+            code, info = s.solve(B, X, wl.tol, 0, wl.reorth_period)
+            res[mode]["iters"] += info["iters"]
+            res[mode]["ms"] += info["ms_total"]
+            res[mode]["max_true_resid"] = max(res[mode].get("max_true_resid", 0.0), max(info["true_resid"]))
+            if use:
+                val_loss.append(seedcg.seedcg_guess_loss_grad(s.h, B, X, want_grad=False)[0])
+    out = {"mode": "guess_eval", "workload": args.workload, "lattice": list(f.dims), "kappa": kappa,
+           "precision": prec, "train_pairs": ntr, "eval_pairs": nev, "epochs": args.epochs, "lr": args.lr,
+           "train_loss": loss, "heldout_loss": float(np.mean(val_loss)),
+           "s_data": round(t_data, 1), "s_train": round(t_train, 1),
+           "iters_total_zero": int(sum(res["zero"]["iters"])),
+           "iters_total_guess": int(sum(res["guess"]["iters"])),
+           "ms_solve_zero": round(res["zero"]["ms"], 1), "ms_solve_guess": round(res["guess"]["ms"], 1),
+           "max_true_resid": max(res["zero"]["max_true_resid"], res["guess"]["max_true_resid"])}
+    print(json.dumps(out))
+    s.close()
+
+
 def main():
     args = _args()
+    if args.guess_eval:
+        run_guess_eval(args)
+        return
     if args.sweep:
         run_sweep(args)
         return

@@ -92,6 +92,19 @@ def z2_sources(dims: Dims, n: int, seed: int, field_index: int = 0,
     return (2.0 * bits - 1.0).astype(np.complex128)
 
 
+def guess_weights(seed: int, scale: float = 0.1) -> np.ndarray:
+    """Seeded starting weights of the learned-guess network (flat complex128 [11520]:
+    layers 1 -> 8, 8 -> 8, 8 -> 1, each [9 directions][C_out][C_in][4][4]), complex
+    Gaussian with standard deviation scale / sqrt(9 * C_in * 4) per part."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in ((1, 8), (8, 8), (8, 1)):
+        sd = scale / np.sqrt(9 * ci * 4)
+        shape = (9, co, ci, 4, 4)
+        parts.append((sd * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))).reshape(-1))
+    return np.concatenate(parts)
+
+
 def random_spinors(dims: Dims, n: int, seed: int) -> np.ndarray:
     """Complex Gaussian spinors for operator tests, [n][V][4][3]."""
     rng = np.random.default_rng(seed)
