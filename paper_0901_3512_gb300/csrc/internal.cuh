@@ -106,9 +106,28 @@ inline Geom make_geom(const int dims[4]) {
 // ----------------------------------------------------------------------------
 // device buffers
 // ----------------------------------------------------------------------------
+// Owning device allocation: freed by the destructor (or release()); move-only.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
     void ensure(size_t n) {
         if (n <= bytes) return;
         release();

@@ -52,3 +52,35 @@ def test_dslash_point_source_and_free_field():
         want = np.stack([op.Ddag(e) for e in eta])
         assert rel(host(out), want) <= 1e-14
         s.close()
+
+
+def test_repeated_calls_do_not_leak_device_memory():
+    """Per-call device scratch (operator application, solves, projections) is
+    released when the call returns: free device memory is unchanged after
+    many calls."""
+    need_gpu()
+    import torch
+    dims = (8, 8, 8, 8)
+    s = seedcg.Solver(dims, W.gauge_field(dims, 0.5, 41), 0.18, precision="mixed_vbf16", m_max=64)
+    x = dev(W.random_spinors(dims, 12, 42))
+    y = dev(np.zeros((12,) + x.shape[1:], dtype=np.complex128))
+    X = dev(np.zeros((2,) + x.shape[1:], dtype=np.complex128))
+    for _ in range(2):   # first calls: autotuning, lazily loaded kernels, handle caches
+        s.apply(seedcg.OP_M, x, y, prec=0, multi=1)
+        s.apply(seedcg.OP_D, x, y, prec=1, multi=0)
+        X.zero_()
+        s.solve(x[:2], X, 1e-6, 0, 10, allow_not_converged=True)
+        seedcg.seedcg_project_basis(s.h, 16, 3, x[:3], use_tensor_cores=0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(20):
+        s.apply(seedcg.OP_M, x, y, prec=0, multi=1)
+        s.apply(seedcg.OP_D, x, y, prec=1, multi=0)
+        X.zero_()
+        s.solve(x[:2], X, 1e-6, 0, 10, allow_not_converged=True)
+        seedcg.seedcg_project_basis(s.h, 16, 3, x[:3], use_tensor_cores=0)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    # 20 leaked operator scratches alone would be ~20 x 28 MB
+    assert free1 >= free0 - (32 << 20), (free0, free1)
+    s.close()
