@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import freefield
-from oracle.seedcg import (cg, galerkin_seed, improved_seed_cg, lanczos_extremes, lu_factors,
+from oracle.seedcg import (cg, classic_seed_cg, galerkin_seed, improved_seed_cg, lanczos_extremes, lu_factors,
                            seed_lanczos, tridiag)
 from oracle.wilson import WilsonOperator
 from paper_0901_3512_gb300 import workloads as W
@@ -285,3 +285,33 @@ def test_po_guard_when_orthogonality_is_lost_between_po_steps():
     # the guard never fires while PO keeps the basis orthonormal (k = 10)
     r10 = improved_seed_cg(op.M, B[:2], None, 1e-8, 20000, 10, past_factor=1.0)
     assert not r10.seed.breakdown and r10.seed.m == r10.seed.m_conv
+
+
+def test_classic_repeated_seeding():
+    """The comparison variant (Section 1): every round's seed system runs D-Lanczos
+    from its seeded guess, which is textbook CG from that guess (same iteration
+    count within one); later systems start closer and need fewer iterations than CG
+    from zero; the solutions are the dense solve's within cond(M) * tol."""
+    op, eta, B = _problem(nrhs=4)
+    tol = 1e-9
+    Md = op.dense(WilsonOperator.OP_M)
+    ev = np.linalg.eigvalsh(Md)
+    Xd = np.linalg.solve(Md, B.T).T
+    for mode in ("blocked", "literal"):
+        r = classic_seed_cg(op.M, B, None, tol, 4000, 10, seed_mode=mode)
+        assert r.true_resid.max() <= tol
+        for j in range(4):
+            assert np.linalg.norm(r.X[j] - Xd[j]) <= ev[-1] / ev[0] * tol * np.linalg.norm(Xd[j])
+    # round by round, without PO (D-Lanczos is then CG): the seeded guesses of round j,
+    # then textbook CG from them needs the same number of iterations
+    nopo = classic_seed_cg(op.M, B, None, tol, 4000, 0)
+    X = np.zeros_like(B)
+    for j in range(4):
+        start = X[j:] if j > 0 else None
+        res = seed_lanczos(op.M, B[j:], start, tol, 4000, 0, 1.0)
+        textbook = cg(op.M, B[j], None if start is None else start[0], tol, 4000).iters
+        assert abs(res.m - textbook) <= 2, (j, res.m, textbook)
+        assert res.m == nopo.lanczos_iters[j]
+        X[j:] = galerkin_seed(res.V, res.alpha, res.beta, res.R0, start)
+    plain = [cg(op.M, B[j], None, tol, 4000).iters for j in range(4)]
+    assert all(nopo.lanczos_iters[j] < plain[j] for j in range(1, 4))
