@@ -55,6 +55,9 @@ def _args():
                    help="write this run's work units (m, CG iterations) for the reference arm")
     p.add_argument("--compare-fp64", action="store_true",
                    help="also time one plain FP64 solve of the same workload (slow)")
+    p.add_argument("--compare-classic", action="store_true",
+                   help="also time classic repeated seeding (seed_mode 2, Section 1's comparison "
+                        "variant) on the same workload, reported beside the line")
     p.add_argument("--tc-po", type=int, default=1, choices=[0, 1, 2],
                    help="with --only po: use_tensor_cores for the bf16 basis (0 SIMT, 1 default: "
                         "tcgen05 for the seeds only, 2 tcgen05 for the PO projection too)")
@@ -424,6 +427,24 @@ def run_ours(args):
                     "ms_cg": i64["ms_cg"], "speedup_mixed_over_fp64": t64 / (ms_max / 1000.0)}
         s64.close()
 
+    classic_cmp = None
+    if args.compare_classic and rank == 0:
+        sc = seedcg.Solver(f.dims, gauge, kappa, precision=prec, m_max=args.m_max, seed_mode=2)
+        Xc = torch.zeros_like(B)
+        sc.solve(B, Xc, wl.tol, 0, k, stream=stream, allow_not_converged=True)   # warm-up
+        Xc.zero_()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        cc, ic = sc.solve(B, Xc, wl.tol, 0, k, stream=stream, allow_not_converged=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        tc = ea.elapsed_time(eb) / 1000.0
+        classic_cmp = {"seconds": tc, "status": cc, "iters": ic["iters"],
+                       "matvecs_total": int(sum(ic["matvecs"])),
+                       "max_true_resid": max(ic["true_resid"]), "ms_po": ic["ms_po"],
+                       "speedup_improved_over_classic": tc / (ms_max / 1000.0)}
+        sc.close()
+
     if args.record_units and rank == 0:
         units_path = os.path.join(ROOT, "paper_0901_3512_gb300", "workload_units.json")
         table = json.load(open(units_path)) if os.path.exists(units_path) else {}
@@ -457,6 +478,8 @@ def run_ours(args):
                "e2e": e2e, "cpu_baseline": cpu}
         if fp64_cmp:
             out["fp64_plain"] = fp64_cmp
+        if classic_cmp is not None:
+            out["classic_seeding"] = classic_cmp
         print(json.dumps(out))
     s.close()
     if world > 1:

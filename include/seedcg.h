@@ -71,7 +71,12 @@ typedef struct {
                               iterated residual fell by this factor (default 0.1)      */
     int po_passes;         /* 1 = classical Gram-Schmidt, 2 = CGS2 (default 1)         */
     int seed_mode;         /* 0 = literal per-iteration updates (Algorithm 1 steps 3-7;
-                              FP64 only), 1 = blocked Eq. (1) after the Lanczos run    */
+                              FP64 only), 1 = blocked Eq. (1) after the Lanczos run,
+                              2 = classic repeated seeding, the comparison variant of
+                              Section 1: each system in turn is run by Lanczos from its
+                              current guess to convergence (past_factor and extra_iters
+                              are not used) and seeds the systems after it by Eq. (1);
+                              CG then finishes any system still above tol              */
     int x0_given;          /* 1: X holds initial guesses x_0^j on entry                */
     int cg_maxiter;        /* CG iteration cap per system (default 20000)               */
     int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */

@@ -1025,6 +1025,87 @@ seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const dou
 
 namespace {
 
+// Classic repeated seeding (seed_mode 2, the comparison variant of Section 1):
+// round j runs Lanczos on system j from its current guess, stopped at
+// convergence, and seeds systems j+1.. by Eq. (1); then one batched CG finishes
+// every system whose true residual is still above tol.
+template <typename R, typename VT>
+seedcg_status classic_rounds(seedcg_handle* h, int nrhs, double2* B64, double2* X64, double tol,
+                             int k_po, seedcg_info* info, cudaStream_t st) {
+    const long n = 12L * h->g.vol;
+    const seedcg_options saved = h->opt;
+    const bool x0 = saved.x0_given || h->force_x0;
+    std::vector<int> lz(nrhs, 0);
+    float ms_lz = 0.f, ms_po = 0.f, ms_seed = 0.f, ms_rounds = 0.f;
+    int m_conv0 = 0, m0 = 0, po0 = 0;
+    seedcg_status code = SEEDCG_OK;
+    try {
+        h->opt.past_factor = 1.0;
+        h->opt.seed_mode = 1;
+        h->opt.x0_given = 0;
+        for (int j = 0; j < nrhs && code == SEEDCG_OK; j++) {
+            h->force_x0 = x0 || j > 0;
+            const int nr = nrhs - j;
+            std::vector<int> it(nr), mv(nr);
+            std::vector<double> tr(nr);
+            seedcg_info ri{};
+            ri.iters = it.data();
+            ri.matvecs = mv.data();
+            ri.true_resid = tr.data();
+            code = run_solve<R, VT>(h, nr, B64 + (size_t)j * n, X64 + (size_t)j * n, tol, 0, k_po, &ri, st,
+                                    false);
+            lz[j] = ri.m;
+            if (j == 0) {
+                m_conv0 = ri.m_conv;
+                m0 = ri.m;
+                po0 = ri.po_count;
+            }
+            ms_lz += ri.ms_lanczos;
+            ms_po += ri.ms_po;
+            ms_seed += ri.ms_seed;
+            ms_rounds += ri.ms_total;
+        }
+    } catch (...) {
+        h->opt = saved;
+        h->force_x0 = false;
+        throw;
+    }
+    h->opt = saved;
+    h->force_x0 = false;
+    if (code != SEEDCG_OK) return code;
+    CgResult cgr;
+    PhaseTimer t_cg;
+    t_cg.start(st);
+    std::vector<CgGroup> gs{{h, nrhs, B64, X64}};
+    const int poll = saved.poll_every > 0 ? saved.poll_every : 32;
+    batched_cg<R>(gs, tol, sizeof(R) == 8 ? 0.0 : saved.reliable_delta, saved.cg_maxiter, poll, true,
+                  h->cgbuf, h->pinned, cgr, st);
+    t_cg.stop(st);
+    for (int j = 0; j < nrhs; j++)
+        if (cgr.notconv[0][j] || !(cgr.true_resid[0][j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
+    if (info) {
+        info->m_conv = m_conv0;
+        info->m = m0;
+        info->po_count = po0;
+        int mx = 0;
+        for (int j = 0; j < nrhs; j++) mx = std::max(mx, cgr.iters[0][j]);
+        info->cg_iters_max = mx;
+        info->reliable_updates = cgr.reliable_updates;
+        for (int j = 0; j < nrhs; j++) {
+            if (info->iters) info->iters[j] = lz[j] + cgr.iters[0][j];
+            if (info->matvecs)
+                info->matvecs[j] = 2 * lz[j] + ((x0 || j > 0) ? 2 : 0) + 2 * (cgr.iters[0][j] + cgr.ru[0][j]);
+            if (info->true_resid) info->true_resid[j] = cgr.true_resid[0][j];
+        }
+        info->ms_lanczos = ms_lz;
+        info->ms_po = ms_po;
+        info->ms_seed = ms_seed;
+        info->ms_cg = t_cg.read();
+        info->ms_total = ms_rounds + info->ms_cg;
+    }
+    return code;
+}
+
 // ratio[j] = ||eta_j - D x_j|| / ||eta_j|| in FP64 (T: scratch of nrhs fields)
 void d_residuals(seedcg_handle* h, int nrhs, const double2* E64, const double2* X64, double2* T64,
                  std::vector<double>& ratio, cudaStream_t st) {
@@ -1167,7 +1248,19 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
         h->force_x0 = true;
     }
     seedcg_status code;
-    switch (h->opt.precision) {
+    if (h->opt.seed_mode == 2) {
+        switch (h->opt.precision) {
+            case SEEDCG_FP64:
+                code = classic_rounds<double, double2>(h, nrhs, B64, X64, tol, reorth_period, info, st);
+                break;
+            case SEEDCG_MIXED_V32:
+                code = classic_rounds<float, float2>(h, nrhs, B64, X64, tol, reorth_period, info, st);
+                break;
+            default:
+                code = classic_rounds<float, __nv_bfloat162>(h, nrhs, B64, X64, tol, reorth_period, info, st);
+                break;
+        }
+    } else switch (h->opt.precision) {
         case SEEDCG_FP64:
             code = run_solve<double, double2>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
             break;

@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.seedcg import improved_seed_cg, seed_lanczos, galerkin_seed
+from oracle.seedcg import classic_seed_cg, improved_seed_cg, seed_lanczos, galerkin_seed
 from oracle.wilson import WilsonOperator
 from paper_0901_3512_gb300 import seedcg, workloads as W
 from tests.gpu_helpers import dev, host, need_gpu, rel
@@ -279,4 +279,28 @@ def test_original_system_residual_is_binding(precision):
         assert rd <= TOL, (j, rd)
         assert abs(info["true_resid_D"][j] - rd) <= 1e-3 * rd + 1e-15
         assert rel(got[j], Xd[j]) <= cond_d * TOL
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_v32"])
+def test_classic_repeated_seeding_matches_oracle(precision):
+    """seed_mode = 2, the comparison variant of Section 1, against the oracle's
+    classic_seed_cg: every true residual <= tol; in FP64 the per-system iteration
+    counts within 2 % and the solutions within 1e-6 of the oracle's."""
+    need_gpu()
+    dims, u, kappa, op, eta, B, wl = _tiny()
+    ref = classic_seed_cg(op.M, B, None, TOL, 4000, wl.reorth_period)
+    s = seedcg.Solver(dims, u, kappa, precision=precision, seed_mode=2)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(_gpu_B(s, eta), X, TOL, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X).reshape(len(eta), -1)
+    for j in range(len(eta)):
+        tr = np.linalg.norm(B[j] - op.M(got[j])) / np.linalg.norm(B[j])
+        assert tr <= TOL and info["true_resid"][j] <= TOL
+        if precision == "fp64":
+            assert rel(got[j], ref.X[j]) <= 1e-6
+            assert _within(info["iters"][j], int(ref.iters[j])), (j, info["iters"], ref.iters)
+    # the first round is the seed system's own Lanczos run to convergence
+    assert _within(info["m"], int(ref.lanczos_iters[0]))
     s.close()
