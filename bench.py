@@ -240,8 +240,9 @@ def run_batch(args):
     """Several uneven gauge fields in one seedcg_batch_solve (one step = one call)."""
     import torch
 
-    from paper_0901_3512_gb300 import seedcg, workloads as W
+    from paper_0901_3512_gb300 import replicas, seedcg, workloads as W
     world, rank, local = _dist()
+    replicas.init("nccl", torch.device("cuda", local))
     torch.cuda.set_device(local)
     wl = W.WORKLOADS[args.workload]
     prec = args.precision or wl.precision
@@ -259,6 +260,8 @@ def run_batch(args):
     for _ in range(args.warmup):
         seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period)
     torch.cuda.synchronize()
+    replicas.barrier()
+    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     l0 = seedcg.seedcg_kernel_launches()
@@ -268,9 +271,15 @@ def run_batch(args):
         code, infos = seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period)
     e1.record()
     torch.cuda.synchronize()
+    replicas.barrier()
+    torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    out = {"metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": 1, "steps": args.steps,
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, torch.device("cuda", local))
+    if rank != 0:
+        replicas.finish()
+        return
+    out = {"metric": METRIC, "value": replicas.job_seconds_per_solve(ms / 1000.0, world), "unit": "s",
+           "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": {"workload": args.workload,
@@ -286,18 +295,17 @@ def run_batch(args):
     print(json.dumps(out))
     for s in solvers:
         s.close()
+    replicas.finish()
 
 
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    from paper_0901_3512_gb300 import seedcg, workloads as W
+    from paper_0901_3512_gb300 import replicas, seedcg, workloads as W
 
     world, rank, local = _dist()
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init("nccl", torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = W.WORKLOADS[args.workload]
@@ -315,9 +323,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     k = wl.reorth_period
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = replicas.barrier
 
     for _ in range(args.warmup):
         s.solve(B, X, wl.tol, 0, k, stream=stream)
@@ -341,10 +347,7 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = seedcg.seedcg_kernel_launches() - l0
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.max_over_ranks(ms, dev)
     code, info = infos[-1]
     ok = all(c == 0 for c, _ in infos) and max(info["true_resid"]) <= wl.tol
 
@@ -394,12 +397,9 @@ def run_ours(args):
             s.solve(Bh, Xh, wl.tol, 0, k)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         nb = Bh.numel() * Bh.element_size()
-        e2e = {"value": float(tt.item()) / world, "unit": "s", "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb}
+        e2e = {"value": replicas.job_seconds_per_solve(replicas.max_over_ranks(e2e_s, dev), world),
+               "unit": "s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -455,7 +455,7 @@ def run_ours(args):
             json.dump(table, fh, indent=1, sort_keys=True)
 
     if rank == 0:
-        out = {"metric": METRIC, "value": ms_max / 1000.0 / world, "unit": "s",
+        out = {"metric": METRIC, "value": replicas.job_seconds_per_solve(ms_max / 1000.0, world), "unit": "s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None,
@@ -482,8 +482,7 @@ def run_ours(args):
             out["classic_seeding"] = classic_cmp
         print(json.dumps(out))
     s.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def run_only(args):
