@@ -255,6 +255,17 @@ seedcg_status seedcg_guess_predict(seedcg_handle* h, int n, const double* B, dou
 seedcg_status seedcg_time_dslash(seedcg_handle* h, int prec, int n, int reps, int flush_l2,
                                  float* ms_per_launch, void* stream);
 
+/*
+ * Failure-detection self-check (no counterpart in the paper): one thread waits
+ * on an mbarrier that nothing arrives at, through the bounded wait that the
+ * tensor-core kernels use for every mbarrier, with a limit of limit_ms (0, 1000]
+ * milliseconds instead of their 1 s.  *kernel_status receives what the kernel
+ * reports: SEEDCG_ERR_TIMEOUT when the wait gave up as it must.  Returns
+ * SEEDCG_OK when the launch ran and the status was read (the context stays
+ * usable), SEEDCG_ERR_ARG for a bad limit or NULL pointer.
+ */
+seedcg_status seedcg_selftest_bounded_wait(double limit_ms, int* kernel_status);
+
 /* Number of CUDA kernels this library has launched in this process (all
    handles, all threads); differences around a call count its launches. */
 unsigned long long seedcg_kernel_launches(void);

@@ -64,14 +64,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
-// bounded wait: false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait: false once `limit_ns` of globaltimer have passed
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > WAIT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, WAIT_NS);
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
@@ -431,6 +434,19 @@ void launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int rows, long kele
     launch_tc_shape<NB, 4, 1>(ma, mb, rows, kelems, part, part_elems, err, nsplit_out, st);
 }
 
+// Failure-detection self-check: one thread waits on an mbarrier that nothing
+// arrives at, through the bounded wait every tensor-core kernel uses; the wait
+// must give up after limit_ns and the kernel report SEEDCG_ERR_TIMEOUT.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *status = mbar_wait_for(&bar, 0u, limit_ns) ? SEEDCG_OK : SEEDCG_ERR_TIMEOUT;
+}
+
 }  // namespace
 
 size_t tc_b_bytes(long n, int nvec) {
@@ -470,3 +486,17 @@ void tc_project(const __nv_bfloat162* V, int rows_alloc, int rows, const float2*
 }
 
 }  // namespace seedcg
+
+extern "C" seedcg_status seedcg_selftest_bounded_wait(double limit_ms, int* kernel_status) {
+    if (!kernel_status || !(limit_ms > 0.0) || limit_ms > 1000.0) return SEEDCG_ERR_ARG;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return SEEDCG_ERR_OOM;
+    const int init = 1;
+    cudaMemcpy(d, &init, sizeof(int), cudaMemcpyHostToDevice);
+    seedcg::k_wait_selftest<<<1, 32>>>((unsigned long long)(limit_ms * 1e6), d);
+    seedcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(kernel_status, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? SEEDCG_OK : SEEDCG_ERR_CUDA;
+}

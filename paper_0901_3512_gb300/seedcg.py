@@ -62,7 +62,7 @@ EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "see
            "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
            "seedcg_project_basis", "seedcg_batch_solve", "seedcg_guess_set_weights",
            "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
-           "seedcg_guess_predict", "seedcg_apply_noalloc"]
+           "seedcg_guess_predict", "seedcg_apply_noalloc", "seedcg_selftest_bounded_wait"]
 GUESS_NW = 11520
 
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_selftest_bounded_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+    lib.seedcg_selftest_bounded_wait.restype = ctypes.c_int
     lib.seedcg_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          vp, vp, vp]
     lib.seedcg_apply_noalloc.restype = ctypes.c_int
@@ -254,6 +256,16 @@ def seedcg_apply_noalloc(h, op: int, prec: int, multi: int, n: int, inp, out, st
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def seedcg_selftest_bounded_wait(limit_ms: float = 20.0) -> int:
+    """Run the bounded-wait self-check; returns the kernel's status
+    (SEEDCG_ERR_TIMEOUT when the wait gave up as it must)."""
+    st = ctypes.c_int(0)
+    code = load().seedcg_selftest_bounded_wait(float(limit_ms), ctypes.byref(st))
+    if code != SEEDCG_OK:
+        raise SeedCGError(code, "bounded-wait self-check could not run")
+    return st.value
 
 
 def seedcg_get_lanczos(h, cap: int):

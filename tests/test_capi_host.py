@@ -60,3 +60,12 @@ def test_solve_and_apply_reject_null_handle():
     assert lib.seedcg_apply(None, 0, 0, 0, 1, None, None, None) == seedcg.SEEDCG_ERR_ARG
     assert b"NULL" in lib.seedcg_last_error(None)
     lib.seedcg_destroy(None)  # no-op
+
+
+def test_bounded_wait_selftest_rejects_bad_limits_before_device_work():
+    lib = seedcg.load()
+    import ctypes
+    st = ctypes.c_int(7)
+    for bad in (0.0, -1.0, 5000.0):
+        assert lib.seedcg_selftest_bounded_wait(bad, ctypes.byref(st)) == seedcg.SEEDCG_ERR_ARG
+    assert lib.seedcg_selftest_bounded_wait(1.0, None) == seedcg.SEEDCG_ERR_ARG
