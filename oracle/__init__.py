@@ -12,7 +12,11 @@ and holds none of the method's arithmetic.
 Modules:
   wilson_ref.c / wilson.py  the Wilson-Dirac operator D, D^dag, M = D^dag D
   seedcg.py                 Algorithm 1 (literal), the eq.-(1) Galerkin seed,
-                            periodic re-orthogonalisation, CG, Lanczos extremes
+                            periodic re-orthogonalisation, CG, classic repeated
+                            seeding, Lanczos extremes
+  evenodd.py                the even-odd preconditioned (odd-site Schur
+                            complement) system of Section 3
+  deflation.py              Ritz pairs of T_m and deflated initial guesses
   freefield.py              closed-form free-field spectrum (a pin)
   guess.py                  the learned initial-guess network, forward/backward
   tune_kappa.py             the script that tunes kappa per gauge field
