@@ -199,6 +199,18 @@ def _dist():
     return world, rank, local
 
 
+def _config(args, wl, world: int) -> dict:
+    """The single-field workload's config, shared by our arm and the reference arm."""
+    from paper_0901_3512_gb300 import workloads as W
+    f = wl.fields[0]
+    return {"workload": args.workload, "lattice": list(f.dims), "nrhs": wl.nrhs[0],
+            "sources": wl.sources, "tol": wl.tol, "reorth_period": wl.reorth_period,
+            "past_factor": wl.past_factor, "precision": args.precision or wl.precision,
+            "kappa": W.kappa_for(f.name),
+            "l2": "inputs larger than L2 (the stored basis V is tens of GB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -227,7 +239,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "nrhs": sum(wl.nrhs), "tol": wl.tol,
+           "config": _config(args, wl, world) if len(wl.fields) == 1 else
+                     {"workload": args.workload, "nrhs": sum(wl.nrhs), "tol": wl.tol,
                       "reorth_period": wl.reorth_period, "past_factor": wl.past_factor},
            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
                             "sample": costs["sample"] + "; scaled by the recorded work units "
@@ -461,11 +474,7 @@ def run_ours(args):
                "vs_baseline": None,
                "dtype": {"fp64": "f64", "mixed_v32": "f32+c64V+f64", "mixed_vbf16": "f32+bf16V+f64"}[prec],
                "data": "synthetic",
-               "config": {"workload": args.workload, "lattice": list(f.dims), "nrhs": nrhs,
-                          "sources": wl.sources, "tol": wl.tol, "reorth_period": k,
-                          "past_factor": wl.past_factor, "precision": prec, "kappa": kappa,
-                          "l2": "inputs larger than L2 (the stored basis V is tens of GB)",
-                          "parallelism": f"replicas x{world}"},
+               "config": _config(args, wl, world),
                "valid": ok,
                "solve": {"m_conv": info["m_conv"], "m": m, "po_count": info["po_count"],
                          "cg_iters_max": info["cg_iters_max"], "iters": info["iters"],

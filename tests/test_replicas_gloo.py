@@ -69,3 +69,24 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
         assert len(lines) == 1 and json.loads(lines[0])["impl"] == "reference"
     else:
         assert lines == []
+
+
+def test_reference_arm_line_contract():
+    """The reference arm (the oracle timed on the host cores) prints one JSON line
+    with the bench contract's keys, on the same config as the GPU arm."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--cpu-sample-iters", "4"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["config"]["workload"] == "large_16x16x16x32_nrhs12"
+    assert d["config"]["lattice"] == [16, 16, 16, 32] and d["config"]["nrhs"] == 12
