@@ -174,6 +174,26 @@ seedcg_status seedcg_apply(seedcg_handle* h, int op, int prec, int multi, int n,
                            const double* in, double* out, void* stream);
 
 /*
+ * Even-odd preconditioned operator (Section 3 solves the even-odd system):
+ * with the sites split by parity (x + y + z + t even / odd; every lattice
+ * extent must be even), the odd-site Schur complement A = 1 - kappa^2 H_oe H_eo,
+ * where D = 1 - kappa H.  Half-lattice vectors are complex128
+ * [n][V/2][4][3] holding the odd sites in lexicographic site order.
+ * op: 0 = A, 1 = A^dag (= gamma5 A gamma5), 2 = A^dag A.  prec: 0 = FP64,
+ * 1 = FP32 arithmetic.  in/out: device pointers that may not alias.
+ * SEEDCG_ERR_ARG for odd extents, host pointers or bad op/prec.
+ */
+seedcg_status seedcg_apply_eo(seedcg_handle* h, int op, int prec, int n, const double* in,
+                              double* out, void* stream);
+/* phi = eta_o + kappa H_oe eta_e, the right-hand side of A x_o = phi for D x = eta.
+   eta: device, full [n][V][4][3]; phi: device, half [n][V/2][4][3]; FP64. */
+seedcg_status seedcg_eo_source(seedcg_handle* h, int n, const double* eta, double* phi, void* stream);
+/* The full solution of D x = eta from x_o: x_e = eta_e + kappa H_eo x_o.
+   x_odd: device, half; eta, x: device, full; FP64. */
+seedcg_status seedcg_eo_reconstruct(seedcg_handle* h, int n, const double* x_odd, const double* eta,
+                                    double* x, void* stream);
+
+/*
  * seedcg_apply for callers that cannot allocate device memory, e.g. a host
  * framework whose caching allocator has reserved the GPU's memory for its own
  * pool, or a caller that cannot afford the allocation and implicit

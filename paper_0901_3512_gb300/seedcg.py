@@ -62,7 +62,8 @@ EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "see
            "seedcg_destroy", "seedcg_kernel_launches", "seedcg_time_dslash",
            "seedcg_project_basis", "seedcg_batch_solve", "seedcg_guess_set_weights",
            "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
-           "seedcg_guess_predict", "seedcg_apply_noalloc", "seedcg_selftest_bounded_wait"]
+           "seedcg_guess_predict", "seedcg_apply_noalloc", "seedcg_selftest_bounded_wait",
+           "seedcg_apply_eo", "seedcg_eo_source", "seedcg_eo_reconstruct"]
 GUESS_NW = 11520
 
 
@@ -103,6 +104,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_apply_eo.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.seedcg_eo_source.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.seedcg_eo_reconstruct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
+    for name in ("seedcg_apply_eo", "seedcg_eo_source", "seedcg_eo_reconstruct"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.seedcg_selftest_bounded_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
     lib.seedcg_selftest_bounded_wait.restype = ctypes.c_int
     lib.seedcg_apply_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -256,6 +262,28 @@ def seedcg_apply_noalloc(h, op: int, prec: int, multi: int, n: int, inp, out, st
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+EO_A, EO_ADAG, EO_MEO = 0, 1, 2
+
+
+def seedcg_apply_eo(h, op: int, prec: int, inp, out, stream=None):
+    """Even-odd operator on half-lattice (odd-site) vectors: A, A^dag or A^dag A."""
+    n = inp.shape[0]
+    _check(h, load().seedcg_apply_eo(h, int(op), int(prec), int(n), ctypes.c_void_p(_ptr(inp)),
+                                     ctypes.c_void_p(_ptr(out)), _stream_ptr(stream)))
+
+
+def seedcg_eo_source(h, eta, phi, stream=None):
+    """phi = eta_o + kappa H_oe eta_e (full eta -> half phi)."""
+    _check(h, load().seedcg_eo_source(h, int(eta.shape[0]), ctypes.c_void_p(_ptr(eta)),
+                                      ctypes.c_void_p(_ptr(phi)), _stream_ptr(stream)))
+
+
+def seedcg_eo_reconstruct(h, x_odd, eta, x, stream=None):
+    """Full solution from the odd sites: x_e = eta_e + kappa H_eo x_o."""
+    _check(h, load().seedcg_eo_reconstruct(h, int(eta.shape[0]), ctypes.c_void_p(_ptr(x_odd)),
+                                           ctypes.c_void_p(_ptr(eta)), ctypes.c_void_p(_ptr(x)),
+                                           _stream_ptr(stream)))
 
 
 def seedcg_selftest_bounded_wait(limit_ms: float = 20.0) -> int:
