@@ -241,6 +241,29 @@ seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const d
                                    double* C, int use_tensor_cores, void* stream);
 
 /*
+ * Host only: the nev smallest eigenpairs of the symmetric tridiagonal matrix
+ * with alpha[0..m-1] on the diagonal and beta[0..m-2] beside it (T_m of Eq. 2's
+ * Lanczos run), by Sturm-sequence bisection and inverse iteration.  theta: nev
+ * ascending values; S: row-major [m][nev], S[a*nev + j] = entry a of eigenvector
+ * j (unit length).  SEEDCG_ERR_ARG for bad sizes or NULL pointers.
+ */
+seedcg_status seedcg_tridiag_lowest(int m, const double* alpha, const double* beta, int nev, double* theta,
+                                   double* S);
+
+/*
+ * Deflated initial guesses from the last solve's stored basis (the premise of
+ * Sections 1-2: the basis built past convergence holds accurate low
+ * eigenvectors).  The nev (<= 64) smallest Ritz pairs (theta_j, y_j = V s_j) of
+ * T_m give, for each of nr new right-hand sides b (same gauge field), the
+ * Galerkin guess x0 = Y c with (Y^dag M Y) c = Y^dag b, in FP64.  B, X0: device,
+ * complex128 [nr][V][4][3]; ritz_values: host, nev doubles, or NULL.  Pass X0
+ * with x0_given = 1 to a later seedcg_solve.  SEEDCG_ERR_BREAKDOWN if Y^dag M Y
+ * is not positive definite.
+ */
+seedcg_status seedcg_deflate_guess(seedcg_handle* h, int nev, int nr, const double* B, double* X0,
+                                   double* ritz_values, void* stream);
+
+/*
  * Learned initial guess (the project's extension; the paper has none): a
  * gauge-covariant nearest-neighbour network of three layers, 1 -> 8 -> 8 -> 1
  * channels,

@@ -345,6 +345,36 @@ seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* o
     }
 }
 
+seedcg_status seedcg_tridiag_lowest(int m, const double* alpha, const double* beta, int nev, double* theta,
+                                   double* S) {
+    if (m < 1 || nev < 1 || nev > m || !alpha || (m > 1 && !beta) || !theta || !S) return SEEDCG_ERR_ARG;
+    try {
+        seedcg::tridiag_lowest(m, alpha, beta, nev, theta, S);
+        return SEEDCG_OK;
+    } catch (...) {
+        return SEEDCG_ERR_ARG;
+    }
+}
+
+seedcg_status seedcg_deflate_guess(seedcg_handle* h, int nev, int nr, const double* B, double* X0,
+                                   double* ritz_values, void* stream) {
+    if (!h || !B || !X0) return fail(h, SEEDCG_ERR_ARG, "h, B or X0 is NULL");
+    if (h->vbasis_m < 1) return fail(h, SEEDCG_ERR_ARG, "no stored basis: run seedcg_solve first");
+    if (nev < 1 || nev > 64 || nev > h->vbasis_m || nr < 1 || nr > 256)
+        return fail(h, SEEDCG_ERR_ARG, "nev must be in [1, min(64, basis size)], nr in [1, 256]");
+    if (!is_device_ptr(B) || !is_device_ptr(X0)) return fail(h, SEEDCG_ERR_ARG, "B and X0 must be device pointers");
+    try {
+        SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
+        seedcg_status c = seedcg::deflate_impl(h, nev, nr, B, X0, ritz_values,
+                                               reinterpret_cast<cudaStream_t>(stream));
+        if (c == SEEDCG_ERR_BREAKDOWN) h->err = "the Ritz Gram matrix Y^dag M Y is not positive definite";
+        else if (c == SEEDCG_ERR_ARG) h->err = "bad nev or basis";
+        return c;
+    } catch (const Error& e) {
+        return fail(h, e.code, e.msg);
+    }
+}
+
 seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const double* X,
                                    double* C, int use_tensor_cores, void* stream) {
     if (!h || !X || !C) return fail(h, SEEDCG_ERR_ARG, "h, X or C is NULL");

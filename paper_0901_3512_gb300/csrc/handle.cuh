@@ -51,6 +51,9 @@ bool guess_ready(const seedcg_handle* h);
 seedcg_status batch_solve_impl(seedcg_handle** hs, int nf, const int* nrhs, const double* const* B,
                                double* const* X, double tol, int extra_iters, int reorth_period,
                                seedcg_info* infos, cudaStream_t st);
+void tridiag_lowest(int m, const double* a, const double* b, int nev, double* theta, double* S);
+seedcg_status deflate_impl(seedcg_handle* h, int nev, int nr, const double* B, double* X0, double* theta_out,
+                           cudaStream_t st);
 seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const double* X,
                                  double* C, int use_tc, cudaStream_t st);
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,

@@ -8,6 +8,7 @@
 //            reliable updates in the mixed-precision modes.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstddef>
 #include <cstring>
 #include <vector>
@@ -974,6 +975,160 @@ seedcg_status batch_solve_impl(seedcg_handle** hs, int nf, const int* nrhs, cons
     }
     SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
     return code;
+}
+
+// ---------------------------------------------------------------------------
+// Ritz pairs and deflated initial guesses from the stored basis (the premise of
+// Sections 1-2: the subspace built past convergence holds accurate low
+// eigenvectors of M).
+// ---------------------------------------------------------------------------
+
+// number of eigenvalues of the symmetric tridiagonal T below x (Sturm sequence
+// of the LDL^T factorisation of T - x I)
+static int sturm_count(int m, const double* a, const double* b, double x) {
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; i++) {
+        const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+        d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) c++;
+    }
+    return c;
+}
+
+void tridiag_lowest(int m, const double* a, const double* b, int nev, double* theta, double* S) {
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < m; i++) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i < m - 1 ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const double scale = std::max(std::fabs(lo), std::fabs(hi));
+    // eigenvalues by bisection: theta_k is where the count passes k
+    for (int k = 0; k < nev; k++) {
+        double l = lo, u = hi;
+        for (int it = 0; it < 200 && u - l > 4e-16 * scale; it++) {
+            const double mid = 0.5 * (l + u);
+            if (sturm_count(m, a, b, mid) <= k) l = mid;
+            else u = mid;
+        }
+        theta[k] = 0.5 * (l + u);
+    }
+    // eigenvectors by inverse iteration with a slightly shifted theta, then
+    // Gram-Schmidt against the earlier vectors (clusters)
+    std::vector<double> y(m), z(m), dd(m), cc(m);
+    for (int k = 0; k < nev; k++) {
+        const double sh = theta[k] - 1e-13 * scale;
+        for (int i = 0; i < m; i++) y[i] = 1.0 / std::sqrt((double)m) * (1.0 + 0.01 * ((i * 7 + k * 13) % 11));
+        for (int it = 0; it < 4; it++) {
+            // solve (T - sh I) z = y by elimination without pivoting (tiny pivots floored)
+            for (int i = 0; i < m; i++) {
+                double piv = a[i] - sh - (i > 0 ? b[i - 1] * cc[i - 1] : 0.0);
+                if (std::fabs(piv) < 1e-300) piv = 1e-300;
+                cc[i] = i < m - 1 ? b[i] / piv : 0.0;
+                dd[i] = (y[i] - (i > 0 ? b[i - 1] * dd[i - 1] : 0.0)) / piv;
+            }
+            z[m - 1] = dd[m - 1];
+            for (int i = m - 2; i >= 0; i--) z[i] = dd[i] - cc[i] * z[i + 1];
+            for (int j = 0; j < k; j++) {
+                double p = 0.0;
+                for (int i = 0; i < m; i++) p += S[(size_t)i * nev + j] * z[i];
+                for (int i = 0; i < m; i++) z[i] -= p * S[(size_t)i * nev + j];
+            }
+            double nrm = 0.0;
+            for (int i = 0; i < m; i++) nrm += z[i] * z[i];
+            nrm = std::sqrt(nrm);
+            for (int i = 0; i < m; i++) y[i] = z[i] / nrm;
+        }
+        for (int i = 0; i < m; i++) S[(size_t)i * nev + k] = y[i];
+    }
+}
+
+seedcg_status deflate_impl(seedcg_handle* h, int nev, int nr, const double* B, double* X0, double* theta_out,
+                           cudaStream_t st) {
+    const int vol = h->g.vol;
+    const long n = 12L * vol;
+    const int m = std::min<int>(h->vbasis_m, (int)h->alpha.size());
+    if (m < 1 || nev < 1 || nev > m || nev > 64 || nr < 1) return SEEDCG_ERR_ARG;
+    std::vector<double> theta(nev), S((size_t)m * nev);
+    tridiag_lowest(m, h->alpha.data(), h->beta.data(), nev, theta.data(), S.data());
+    std::vector<double2> hc((size_t)m * nev);
+    for (size_t i = 0; i < hc.size(); i++) hc[i] = make_double2(S[i], 0.0);
+    DevBuf cbuf, ybuf, mybuf, tbuf, bbuf, gbuf, rbuf, xbuf, scr;
+    cbuf.ensure(hc.size() * sizeof(double2));
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(cbuf.p, hc.data(), hc.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    const size_t fy = (size_t)nev * n * sizeof(double2);
+    ybuf.ensure(fy);
+    mybuf.ensure(fy);
+    tbuf.ensure(fy);
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(ybuf.p, 0, fy, st));
+    double2* Y = ybuf.as<double2>();
+    // Ritz vectors Y = V S in FP64
+    if (h->vbasis_prec == SEEDCG_FP64)
+        gemm_n<double, double2, double2>(h->vbasis.as<double2>(), n, m, cbuf.as<double2>(), nev, nev, Y, n, n,
+                                         1.0, st);
+    else if (h->vbasis_prec == SEEDCG_MIXED_V32)
+        gemm_n<float, float2, double2>(h->vbasis.as<float2>(), n, m, cbuf.as<double2>(), nev, nev, Y, n, n,
+                                       1.0, st);
+    else
+        gemm_n<float, __nv_bfloat162, double2>(h->vbasis.as<__nv_bfloat162>(), n, m, cbuf.as<double2>(), nev,
+                                               nev, Y, n, n, 1.0, st);
+    apply_M64(h, nev, Y, tbuf.as<double2>(), mybuf.as<double2>(), st);
+    const size_t split = std::max<size_t>((size_t)nev * std::max(nev, nr) * 64, (size_t)1 << 20);
+    scr.ensure(split * sizeof(double2));
+    gbuf.ensure((size_t)nev * nev * sizeof(double2));
+    gemm_t<double, double2>(Y, n, nev, mybuf.as<double2>(), n, nev, n, gbuf.as<double2>(), nev, scr.as<double2>(),
+                            split, st);                                          // G = Y^dag M Y
+    bbuf.ensure((size_t)nr * n * sizeof(double2));
+    to_internal_f64(B, bbuf.as<double2>(), vol, nr, st);
+    rbuf.ensure((size_t)nev * nr * sizeof(double2));
+    gemm_t<double, double2>(Y, n, nev, bbuf.as<double2>(), n, nr, n, rbuf.as<double2>(), nr, scr.as<double2>(),
+                            split, st);                                          // R = Y^dag B
+    std::vector<double2> G((size_t)nev * nev), Rh((size_t)nev * nr);
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(G.data(), gbuf.p, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(Rh.data(), rbuf.p, Rh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    // Cholesky G = L L^dag (Hermitian positive definite), then c = G^-1 R column by column
+    using cd = std::complex<double>;
+    std::vector<cd> L((size_t)nev * nev, cd(0, 0));
+    for (int i = 0; i < nev; i++)
+        for (int j = 0; j <= i; j++) {
+            cd sum(G[(size_t)i * nev + j].x, G[(size_t)i * nev + j].y);
+            for (int k = 0; k < j; k++) sum -= L[(size_t)i * nev + k] * std::conj(L[(size_t)j * nev + k]);
+            if (i == j) {
+                if (!(sum.real() > 0.0)) return SEEDCG_ERR_BREAKDOWN;
+                L[(size_t)i * nev + i] = std::sqrt(sum.real());
+            } else {
+                L[(size_t)i * nev + j] = sum / L[(size_t)j * nev + j];
+            }
+        }
+    std::vector<double2> hcoef((size_t)nev * nr);
+    std::vector<cd> w(nev);
+    for (int r = 0; r < nr; r++) {
+        for (int i = 0; i < nev; i++) {
+            cd sum(Rh[(size_t)i * nr + r].x, Rh[(size_t)i * nr + r].y);
+            for (int k = 0; k < i; k++) sum -= L[(size_t)i * nev + k] * w[k];
+            w[i] = sum / L[(size_t)i * nev + i];
+        }
+        for (int i = nev - 1; i >= 0; i--) {
+            cd sum = w[i];
+            for (int k = i + 1; k < nev; k++) sum -= std::conj(L[(size_t)k * nev + i]) * w[k];
+            w[i] = sum / L[(size_t)i * nev + i];
+        }
+        for (int i = 0; i < nev; i++) hcoef[(size_t)i * nr + r] = make_double2(w[i].real(), w[i].imag());
+    }
+    DevBuf cc;
+    cc.ensure(hcoef.size() * sizeof(double2));
+    SEEDCG_CUDA_TRY(cudaMemcpyAsync(cc.p, hcoef.data(), hcoef.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    xbuf.ensure((size_t)nr * n * sizeof(double2));
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(xbuf.p, 0, (size_t)nr * n * sizeof(double2), st));
+    gemm_n<double, double2, double2>(Y, n, nev, cc.as<double2>(), nr, nr, xbuf.as<double2>(), n, n, 1.0, st);
+    from_internal_f64(xbuf.as<double2>(), X0, vol, nr, st);
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (theta_out)
+        for (int k = 0; k < nev; k++) theta_out[k] = theta[k];
+    return SEEDCG_OK;
 }
 
 seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const double* X,

@@ -63,7 +63,8 @@ EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "see
            "seedcg_project_basis", "seedcg_batch_solve", "seedcg_guess_set_weights",
            "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
            "seedcg_guess_predict", "seedcg_apply_noalloc", "seedcg_selftest_bounded_wait",
-           "seedcg_apply_eo", "seedcg_eo_source", "seedcg_eo_reconstruct"]
+           "seedcg_apply_eo", "seedcg_eo_source", "seedcg_eo_reconstruct", "seedcg_tridiag_lowest",
+           "seedcg_deflate_guess"]
 GUESS_NW = 11520
 
 
@@ -104,6 +105,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_tridiag_lowest.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
+    lib.seedcg_tridiag_lowest.restype = ctypes.c_int
+    lib.seedcg_deflate_guess.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+    lib.seedcg_deflate_guess.restype = ctypes.c_int
     lib.seedcg_apply_eo.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.seedcg_eo_source.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.seedcg_eo_reconstruct.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp]
@@ -264,6 +269,32 @@ def seedcg_apply_noalloc(h, op: int, prec: int, multi: int, n: int, inp, out, st
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 EO_A, EO_ADAG, EO_MEO = 0, 1, 2
+
+
+def seedcg_tridiag_lowest(alpha, beta, nev: int):
+    """Host: the nev smallest eigenpairs of tridiag(beta, alpha, beta); returns
+    (theta [nev], S [m][nev])."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    m = a.size
+    b = np.ascontiguousarray(beta, dtype=np.float64)[:max(m - 1, 1)]
+    theta = np.zeros(nev)
+    S = np.zeros((m, nev))
+    code = load().seedcg_tridiag_lowest(int(m), ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                        int(nev), ctypes.c_void_p(theta.ctypes.data),
+                                        ctypes.c_void_p(S.ctypes.data))
+    if code != SEEDCG_OK:
+        raise SeedCGError(code, "tridiagonal eigensolve rejected its arguments")
+    return theta, S
+
+
+def seedcg_deflate_guess(h, nev: int, B, X0, stream=None):
+    """Deflated initial guesses X0 for the right-hand sides B from the last
+    solve's Ritz vectors; returns the nev Ritz values."""
+    theta = np.zeros(nev)
+    _check(h, load().seedcg_deflate_guess(h, int(nev), int(B.shape[0]), ctypes.c_void_p(_ptr(B)),
+                                          ctypes.c_void_p(_ptr(X0)), ctypes.c_void_p(theta.ctypes.data),
+                                          _stream_ptr(stream)))
+    return theta
 
 
 def seedcg_apply_eo(h, op: int, prec: int, inp, out, stream=None):

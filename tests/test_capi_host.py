@@ -69,3 +69,31 @@ def test_bounded_wait_selftest_rejects_bad_limits_before_device_work():
     for bad in (0.0, -1.0, 5000.0):
         assert lib.seedcg_selftest_bounded_wait(bad, ctypes.byref(st)) == seedcg.SEEDCG_ERR_ARG
     assert lib.seedcg_selftest_bounded_wait(1.0, None) == seedcg.SEEDCG_ERR_ARG
+
+
+def test_tridiag_lowest_matches_scipy():
+    """The host Sturm-bisection / inverse-iteration eigensolver the Ritz deflation
+    uses, against scipy's tridiagonal eigensolver: a random matrix and the T_m of
+    an oracle Lanczos run past convergence."""
+    from scipy.linalg import eigh_tridiagonal
+    from oracle.seedcg import seed_lanczos
+    from oracle.wilson import WilsonOperator
+    from paper_0901_3512_gb300 import workloads as W
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal(300) + 4.0, rng.standard_normal(299)
+    dims = (4, 2, 2, 4)
+    op = WilsonOperator(dims, W.gauge_field(dims, 0.5, 7), 0.2)
+    B = np.stack([op.Ddag(W.z2_sources(dims, 1, 7).reshape(-1))])
+    s = seed_lanczos(op.M, B, None, 1e-10, 4000, 10, 2.0)
+    for alpha, beta in ((a, b), (s.alpha, s.beta[:-1])):
+        nev = 12
+        theta, S = seedcg.seedcg_tridiag_lowest(alpha, beta, nev)
+        ref, Sref = eigh_tridiagonal(alpha, beta, select="i", select_range=(0, nev - 1))
+        scale = np.abs(ref).max() + np.abs(alpha).max()
+        assert np.allclose(theta, ref, rtol=0, atol=1e-12 * scale)
+        assert np.allclose(np.linalg.norm(S, axis=0), 1.0, atol=1e-12)
+        overlap = np.abs(np.sum(S * Sref, axis=0))
+        gaps = np.minimum(np.abs(np.diff(np.r_[-np.inf, ref])), np.abs(np.diff(np.r_[ref, np.inf])))
+        for j in range(nev):
+            if gaps[j] > 1e-8 * scale:
+                assert overlap[j] > 1 - 1e-8, (j, overlap[j], gaps[j])
