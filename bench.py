@@ -72,6 +72,10 @@ def _args():
                    help="learned initial guess on the workload's field: train on (b, x) pairs the "
                         "solver produces, then solve held-out Z2 sources from x0 = 0 and from the "
                         "learned x0 (iterations and time; one JSON line, not a bench line)")
+    p.add_argument("--deflate-eval", type=int, default=0, metavar="NEV",
+                   help="Ritz deflation at the workload's scale: after the solve, a new batch of "
+                        "Z2 sources is solved from x0 = 0 and from the guess deflated with NEV "
+                        "Ritz vectors (one JSON line, not a bench line)")
     p.add_argument("--train-pairs", type=int, default=2000)
     p.add_argument("--eval-pairs", type=int, default=64)
     p.add_argument("--epochs", type=int, default=10)
@@ -632,8 +636,50 @@ def run_guess_eval(args):
     s.close()
 
 
+def run_deflate_eval(args):
+    """Later right-hand sides on the same field: the Seed-CG solve of a new batch
+    from x0 = 0 against the same solve from the Ritz-deflated guess of the first
+    solve's basis."""
+    import time
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[args.workload]
+    f = wl.fields[0]
+    prec = args.precision or wl.precision
+    s = seedcg.Solver(f.dims, f.gauge(), W.kappa_for(f.name), precision=prec, past_factor=wl.past_factor,
+                      m_max=args.m_max)
+    eta = torch.from_numpy(wl.sources_for(0)).cuda()
+    B = torch.empty_like(eta)
+    s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+    X = torch.zeros_like(B)
+    code, info = s.solve(B, X, wl.tol, 0, wl.reorth_period)
+    eta2 = torch.from_numpy(W.z2_sources(f.dims, wl.nrhs[0], f.seed, f.field_index, stream=900)).cuda()
+    B2 = torch.empty_like(eta2)
+    s.apply(seedcg.OP_DDAG, eta2, B2, prec=0, multi=1)
+    X0 = torch.zeros_like(B2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta = seedcg.seedcg_deflate_guess(s.h, args.deflate_eval, B2, X0)
+    torch.cuda.synchronize()
+    t_defl = time.perf_counter() - t0
+    runs = {}
+    for mode, x0 in (("zero", torch.zeros_like(B2)), ("deflated", X0.clone())):
+        s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max,
+                      x0_given=1 if mode == "deflated" else 0)
+        c, i = s.solve(B2, x0, wl.tol, 0, wl.reorth_period)
+        runs[mode] = {"status": c, "ms_total": round(i["ms_total"], 1), "m": i["m"],
+                      "iters_total": int(sum(i["iters"])), "max_true_resid": max(i["true_resid"])}
+    print(json.dumps({"mode": "deflate_eval", "workload": args.workload, "precision": prec, "nev": args.deflate_eval,
+                      "first_solve_m": info["m"], "ritz_values_lowest": [float(t) for t in theta[:4]],
+                      "s_deflation": round(t_defl, 3), "new_batch": runs}))
+    s.close()
+
+
 def main():
     args = _args()
+    if args.deflate_eval:
+        run_deflate_eval(args)
+        return
     if args.guess_eval:
         run_guess_eval(args)
         return
