@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -379,6 +380,14 @@ std::string tune_key(const std::vector<CgGroup>& groups, bool fp64) {
     return k;
 }
 
+// the process-wide table of tuned warps per tile (guarded by tune_mutex); the
+// optional SEEDCG_TUNE_CACHE file is shared with the brick-dslash tuner, so only
+// its "mf_dslash..." lines are read here
+std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 std::vector<std::pair<std::string, int>>& tune_table() {
     static std::vector<std::pair<std::string, int>> t;
     static bool loaded = false;
@@ -388,9 +397,11 @@ std::vector<std::pair<std::string, int>>& tune_table() {
         if (path) {
             FILE* f = fopen(path, "r");
             if (f) {
-                char key[512];
+                char line[640], key[512];
                 int v;
-                while (fscanf(f, "%511s %d", key, &v) == 2) t.push_back({key, v});
+                while (fgets(line, sizeof(line), f))
+                    if (sscanf(line, "%511s %d", key, &v) == 2 && strncmp(key, "mf_dslash", 9) == 0)
+                        t.push_back({key, v});
                 fclose(f);
             }
         }
@@ -402,8 +413,11 @@ template <typename R>
 int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const GroupDev<R>* gdev, int ng,
                  Rows rows, cudaStream_t st) {
     const std::string key = tune_key(groups, sizeof(R) == 8);
-    for (auto& e : tune_table())
-        if (e.first == key) return e.second;
+    {
+        std::lock_guard<std::mutex> lk(tune_mutex());
+        for (auto& e : tune_table())
+            if (e.first == key) return e.second;
+    }
     const int cands[3] = {4, 8, 12};
     cudaEvent_t a, b;
     SEEDCG_CUDA_TRY(cudaEventCreate(&a));
@@ -428,6 +442,7 @@ int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const GroupDev<R
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lk(tune_mutex());
     tune_table().push_back({key, best});
     if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
         FILE* f = fopen(path, "a");

@@ -357,10 +357,12 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
         if (const char* path = getenv("SEEDCG_TUNE_CACHE")) {
             FILE* f = fopen(path, "r");
             if (f) {
-                char k[512];
+                // the file is shared with the batched-CG tuner: read only full brick lines
+                char line[640], k[512];
                 int a, b, c;
-                while (fscanf(f, "%511s %d %d %d", k, &a, &b, &c) == 4)
-                    if (std::string(k) == key) cache[key] = BrickChoice{a, b, c};
+                while (fgets(line, sizeof(line), f))
+                    if (sscanf(line, "%511s %d %d %d", k, &a, &b, &c) == 4 && std::string(k) == key)
+                        cache[key] = BrickChoice{a, b, c};
                 fclose(f);
                 it = cache.find(key);
                 if (it != cache.end()) return it->second;
