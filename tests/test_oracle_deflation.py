@@ -45,3 +45,15 @@ def test_deflated_guess_galerkin_condition_and_gain():
     cold = cg(op.M, b, None, 1e-8, 20000).iters
     warm = cg(op.M, b, x0, 1e-8, 20000).iters
     assert warm < 0.7 * cold, (warm, cold)
+
+
+def test_deflated_guess_galerkin_condition_for_any_basis():
+    """The Galerkin projection holds for a general basis too (a Gram matrix that
+    is neither diagonal nor real), not only for Ritz vectors."""
+    op = WilsonOperator(DIMS, W.gauge_field(DIMS, 0.5, 8), 0.2)
+    rng = np.random.default_rng(9)
+    Y = rng.standard_normal((3, op.n)) + 1j * rng.standard_normal((3, op.n))
+    b = rng.standard_normal(op.n) + 1j * rng.standard_normal(op.n)
+    x0 = deflated_guess(op.M, Y, b)
+    g = Y.conj() @ (b - op.M(x0))
+    assert np.abs(g).max() <= 1e-9 * np.linalg.norm(b) * np.linalg.norm(Y[0])
