@@ -188,6 +188,17 @@ seedcg_status seedcg_apply_eo(seedcg_handle* h, int op, int prec, int n, const d
 /* phi = eta_o + kappa H_oe eta_e, the right-hand side of A x_o = phi for D x = eta.
    eta: device, full [n][V][4][3]; phi: device, half [n][V/2][4][3]; FP64. */
 seedcg_status seedcg_eo_source(seedcg_handle* h, int n, const double* eta, double* phi, void* stream);
+/*
+ * Improved Seed-CG on the even-odd system (Section 3 solves A^dag A x_o = A^dag phi):
+ * for each right-hand side eta (device, full [nrhs][V][4][3]) phi = eta_o + kappa H_oe eta_e,
+ * Algorithm 1 on A^dag A with the handle's options (FP64 only: precision and seed_mode are
+ * not used; blocked Eq. (1) seeds), CG for every system above tol, and the full solution x
+ * (device, full) by x_e = eta_e + kappa H_eo x_o.  The criterion is ||b - A^dag A x_o|| <= tol ||b||,
+ * b = A^dag phi, reported in info->true_resid.  Host-driven: scalars on the host, vectors in
+ * this library's kernels.
+ */
+seedcg_status seedcg_solve_eo(seedcg_handle* h, int nrhs, const double* eta, double* x, double tol,
+                              int extra_iters, int reorth_period, seedcg_info* info, void* stream);
 /* The full solution of D x = eta from x_o: x_e = eta_e + kappa H_eo x_o.
    x_odd: device, half; eta, x: device, full; FP64. */
 seedcg_status seedcg_eo_reconstruct(seedcg_handle* h, int n, const double* x_odd, const double* eta,

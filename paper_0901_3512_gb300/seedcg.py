@@ -64,7 +64,7 @@ EXPORTS = ["seedcg_default_options", "seedcg_create", "seedcg_set_options", "see
            "seedcg_guess_get_weights", "seedcg_guess_loss_grad", "seedcg_guess_train",
            "seedcg_guess_predict", "seedcg_apply_noalloc", "seedcg_selftest_bounded_wait",
            "seedcg_apply_eo", "seedcg_eo_source", "seedcg_eo_reconstruct", "seedcg_tridiag_lowest",
-           "seedcg_deflate_guess"]
+           "seedcg_deflate_guess", "seedcg_solve_eo"]
 GUESS_NW = 11520
 
 
@@ -105,6 +105,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(seedcg_info), vp]
     lib.seedcg_batch_solve.restype = ctypes.c_int
+    lib.seedcg_solve_eo.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(seedcg_info), vp]
+    lib.seedcg_solve_eo.restype = ctypes.c_int
     lib.seedcg_tridiag_lowest.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
     lib.seedcg_tridiag_lowest.restype = ctypes.c_int
     lib.seedcg_deflate_guess.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
@@ -302,6 +305,22 @@ def seedcg_apply_eo(h, op: int, prec: int, inp, out, stream=None):
     n = inp.shape[0]
     _check(h, load().seedcg_apply_eo(h, int(op), int(prec), int(n), ctypes.c_void_p(_ptr(inp)),
                                      ctypes.c_void_p(_ptr(out)), _stream_ptr(stream)))
+
+
+def seedcg_solve_eo(h, eta, X, tol: float, extra_iters: int, reorth_period: int, stream=None,
+                    allow_not_converged: bool = False):
+    """Even-odd preconditioned Improved Seed-CG for D x = eta (full-lattice eta and X on the device)."""
+    nrhs = int(eta.shape[0])
+    info = seedcg_info()
+    iters = (ctypes.c_int * nrhs)()
+    mv = (ctypes.c_int * nrhs)()
+    tr = (ctypes.c_double * nrhs)()
+    info.iters, info.matvecs, info.true_resid = iters, mv, tr
+    code = load().seedcg_solve_eo(h, nrhs, ctypes.c_void_p(_ptr(eta)), ctypes.c_void_p(_ptr(X)), float(tol),
+                                  int(extra_iters), int(reorth_period), ctypes.byref(info), _stream_ptr(stream))
+    _check(h, code, allow=(SEEDCG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return code, {"m_conv": info.m_conv, "m": info.m, "po_count": info.po_count, "iters": list(iters),
+                  "matvecs": list(mv), "true_resid": list(tr), "ms_total": info.ms_total}
 
 
 def seedcg_eo_source(h, eta, phi, stream=None):
