@@ -35,6 +35,19 @@ void* scratch_on(int device) {
     return g_ptr[device];
 }
 
+// True when p is device (or managed) memory of `device`.  Asking the runtime
+// allocates nothing; a host or unregistered pointer must be refused here,
+// before any kernel dereferences it.
+bool on_device(const void* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 }  // namespace
 }  // namespace seedcg
 
@@ -50,6 +63,10 @@ extern "C" seedcg_status seedcg_apply_noalloc(seedcg_handle* h, int op, int prec
     if (n == 0) return SEEDCG_OK;
     if (!in || !out || in == out) {
         h->err = "in/out NULL or aliased";
+        return SEEDCG_ERR_ARG;
+    }
+    if (!seedcg::on_device(in, h->device) || !seedcg::on_device(out, h->device)) {
+        h->err = "seedcg_apply_noalloc: in and out must be device memory of the handle's GPU";
         return SEEDCG_ERR_ARG;
     }
     const int vol = h->g.vol;

@@ -43,3 +43,25 @@ def test_noalloc_rejects_batches_beyond_the_scratch():
     # the largest batch that fits still works
     seedcg.seedcg_apply_noalloc(s.h, seedcg.OP_M, 0, 1, n - 1, x[: n - 1], y[: n - 1])
     s.close()
+
+
+def test_noalloc_rejects_host_memory():
+    """A host array (numpy, or a pinned torch tensor) is refused with
+    SEEDCG_ERR_ARG before any kernel could dereference it."""
+    need_gpu()
+    import torch
+    dims = (4, 4, 4, 8)
+    s = seedcg.Solver(dims, W.gauge_field(dims, 0.5, 33), 0.2)
+    x = W.random_spinors(dims, 2, 50)
+    yd = dev(np.zeros_like(x))
+    for inp, out in ((np.ascontiguousarray(x), yd), (dev(x), np.zeros_like(x)),
+                     (torch.from_numpy(x).pin_memory(), yd)):
+        with pytest.raises(seedcg.SeedCGError) as e:
+            seedcg.seedcg_apply_noalloc(s.h, seedcg.OP_M, 0, 1, 2, inp, out)
+        assert e.value.code == seedcg.SEEDCG_ERR_ARG
+    # the device call still works after the refusals
+    want = dev(np.zeros_like(x))
+    seedcg.seedcg_apply(s.h, seedcg.OP_M, 0, 1, 2, dev(x), want)
+    seedcg.seedcg_apply_noalloc(s.h, seedcg.OP_M, 0, 1, 2, dev(x), yd)
+    assert rel(host(yd), host(want)) <= 1e-13
+    s.close()
