@@ -53,8 +53,12 @@ def _args():
     p.add_argument("--cpu-sample-iters", type=int, default=24)
     p.add_argument("--record-units", action="store_true",
                    help="write this run's work units (m, CG iterations) for the reference arm")
-    p.add_argument("--compare-fp64", action="store_true",
-                   help="also time one plain FP64 solve of the same workload (slow)")
+    p.add_argument("--no-compare", action="store_true",
+                   help="skip the comparators reported beside the line (one plain FP64 seed-CG "
+                        "solve and one standard batched CG from x0 = 0, both untimed by the line)")
+    p.add_argument("--no-cpu-c1", action="store_true",
+                   help="skip the end-to-end oracle run of the 8^3x16 workload on the host cores")
+    p.add_argument("--oracle-c1-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--compare-classic", action="store_true",
                    help="also time classic repeated seeding (seed_mode 2, Section 1's comparison "
                         "variant) on the same workload, reported beside the line")
@@ -193,6 +197,74 @@ def oracle_estimate(costs, m, k, cg_iters_total, nrhs):
     return m * costs["t_lanczos_iter"] + po_rows * costs["t_po_row"] + cg_iters_total * costs["t_cg_iter"]
 
 
+C1_WORKLOAD = "small_8x8x8x16_nrhs12"
+
+
+def oracle_c1_worker():
+    """Run the oracle, as it stands, end to end on the 8^3x16 twelve-point-source
+    workload (Algorithm 1 with blocked Eq. (1) seeds, then CG for every system
+    above tol) and print one JSON line.  Runs in its own process on the cores it
+    was given, so that it can proceed while the GPU arm measures."""
+    import numpy as np
+    from oracle.seedcg import improved_seed_cg
+    from oracle.wilson import WilsonOperator
+    from paper_0901_3512_gb300 import workloads as W
+    wl = W.WORKLOADS[C1_WORKLOAD]
+    f = wl.fields[0]
+    op = WilsonOperator(f.dims, f.gauge(), W.kappa_for(f.name))
+    eta = wl.sources_for(0)
+    B = np.stack([op.Ddag(e) for e in eta]).reshape(len(eta), -1)
+    t0 = time.perf_counter()
+    r = improved_seed_cg(op.M, B, None, wl.tol, 6000, wl.reorth_period, wl.past_factor,
+                         seed_mode="blocked")
+    t = time.perf_counter() - t0
+    print(json.dumps({"seconds": t, "m_conv": int(r.seed.m_conv), "m": int(r.seed.m),
+                      "iters": [int(i) for i in r.iters],
+                      "max_true_resid": float(np.max(r.true_resid))}), flush=True)
+
+
+def start_oracle_c1():
+    """Start the end-to-end oracle run of the 8^3x16 workload in a child process
+    (a fresh interpreter, started before this process touches the GPU) pinned to
+    every host core but the first two, which stay with the GPU arm's launches."""
+    cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+    use = cores[2:] if len(cores) > 4 else cores
+    env = dict(os.environ)
+    n = str(max(len(use), 1))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = n
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    pre = None
+    if use and hasattr(os, "sched_setaffinity"):
+        def pre():
+            os.sched_setaffinity(0, use)
+    proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-c1-worker"],
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                            preexec_fn=pre, cwd=ROOT)
+    return proc, len(use) if use else os.cpu_count()
+
+
+def finish_oracle_c1(handle, timeout_s: float = 900.0):
+    proc, cores = handle
+    try:
+        out, err = proc.communicate(timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
+        return {"workload": C1_WORKLOAD, "error": f"did not finish within {timeout_s:.0f} s",
+                "cores": cores}
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    if proc.returncode != 0 or not lines:
+        return {"workload": C1_WORKLOAD, "error": (err or out).strip().splitlines()[-1:] or "failed",
+                "cores": cores}
+    d = json.loads(lines[-1])
+    d.update({"workload": C1_WORKLOAD, "cores": cores, "kind": "oracle", "unit": "s",
+              "sample": "the whole 8^3x16 twelve-point-source solve (Algorithm 1 + Eq. (1) "
+                        "seeds + CG), end to end, concurrently with the GPU arm"})
+    return d
+
+
 # ---------------------------------------------------------------------------
 # distributed helpers
 # ---------------------------------------------------------------------------
@@ -322,6 +394,12 @@ def run_ours(args):
     from paper_0901_3512_gb300 import replicas, seedcg, workloads as W
 
     world, rank, local = _dist()
+    c1 = None
+    all_cores = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_cpu_c1:
+        c1 = start_oracle_c1()
+        if all_cores and len(all_cores) > 4:
+            os.sched_setaffinity(0, all_cores[:2])
     replicas.init("nccl", torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -379,7 +457,7 @@ def run_ours(args):
     po_s = info["ms_po"] / 1000.0
     po_gbs = po_alg_bytes / po_s / 1e9 if po_s > 0 else None
     # DRAM bytes per algorithmic byte of the PO kernels, from the 1-pass ncu window of this
-    # workload (profiles/po_kernels_bf16_16x16x16x32.md); only for the configuration measured
+    # workload's PO launches; only for the configuration measured
     traffic = (round(PO_DRAM_PER_ALG_BF16 * po_alg_bytes)
                if prec == "mixed_vbf16" and args.workload == "large_16x16x16x32_nrhs12" else None)
     roofline = {"bound": "hbm", "achieved": po_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -418,20 +496,32 @@ def run_ours(args):
         e2e = {"value": replicas.job_seconds_per_solve(replicas.max_over_ranks(e2e_s, dev), world),
                "unit": "s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        costs = oracle_unit_costs(wl, args.cpu_sample_iters)
-        cg_total = sum(info["iters"]) - m
-        est = oracle_estimate(costs, m, k, cg_total, nrhs)
-        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": costs["sample"] + f"; scaled to this run's work units (m={m}, "
-                         f"{len(range(k, m + 1, k))} PO steps, {cg_total} CG iterations)",
-               "per_unit_s": {kk: costs[kk] for kk in ("t_lanczos_iter", "t_po_row", "t_cg_iter")}}
-
     fp64_cmp = None
-    if args.compare_fp64 and rank == 0:
+    cg_only_cmp = None
+    if not args.no_compare and rank == 0 and args.workload == DEFAULT_WORKLOAD:
+        # the same 12 systems by standard batched CG from x0 = 0 (no Lanczos, no seeds):
+        # what seeding buys on this field (untimed by the line)
+        s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max, seed_mode=3)
+        Xc = torch.zeros_like(B)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        cc, ic = s.solve(B, Xc, wl.tol, 0, k, stream=stream, allow_not_converged=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        tcg = ea.elapsed_time(eb) / 1000.0
+        cg_only_cmp = {"seconds": tcg, "status": cc, "iters": ic["iters"],
+                       "max_true_resid": max(ic["true_resid"]),
+                       "reliable_updates": ic["reliable_updates"],
+                       "seeded_over_cg_only_time": (ms_max / 1000.0) / tcg}
+        s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max)
+        del Xc
+        # one plain FP64 Improved Seed-CG solve of the same systems on the GPU, for the
+        # mixed-precision speed-up (the stored FP64 basis takes ~100 GB: the mixed solver's
+        # basis is released first)
+        s.close()
+        torch.cuda.empty_cache()
         s64 = seedcg.Solver(f.dims, gauge, kappa, precision="fp64", past_factor=wl.past_factor,
-                            m_max=args.m_max)
+                            m_max=5000)
         X64 = torch.zeros_like(B)
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record(stream)
@@ -440,12 +530,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         t64 = ea.elapsed_time(eb) / 1000.0
         fp64_cmp = {"seconds": t64, "status": c64, "m_conv": i64["m_conv"], "m": i64["m"],
-                    "max_true_resid": max(i64["true_resid"]), "ms_po": i64["ms_po"],
-                    "ms_cg": i64["ms_cg"], "speedup_mixed_over_fp64": t64 / (ms_max / 1000.0)}
+                    "iters": i64["iters"], "max_true_resid": max(i64["true_resid"]),
+                    "ms_po": i64["ms_po"], "ms_cg": i64["ms_cg"],
+                    "speedup_mixed_over_fp64": t64 / (ms_max / 1000.0)}
         s64.close()
+        del X64
+        torch.cuda.empty_cache()
 
     classic_cmp = None
     if args.compare_classic and rank == 0:
+        torch.cuda.empty_cache()
         sc = seedcg.Solver(f.dims, gauge, kappa, precision=prec, m_max=args.m_max, seed_mode=2)
         Xc = torch.zeros_like(B)
         sc.solve(B, Xc, wl.tol, 0, k, stream=stream, allow_not_converged=True)   # warm-up
@@ -461,6 +555,23 @@ def run_ours(args):
                        "max_true_resid": max(ic["true_resid"]), "ms_po": ic["ms_po"],
                        "speedup_improved_over_classic": tc / (ms_max / 1000.0)}
         sc.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c1_res = finish_oracle_c1(c1) if c1 is not None else None
+        c1 = None
+        if all_cores:
+            os.sched_setaffinity(0, all_cores)
+        costs = oracle_unit_costs(wl, args.cpu_sample_iters)
+        cg_total = sum(info["iters"]) - m
+        est = oracle_estimate(costs, m, k, cg_total, nrhs)
+        cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": costs["sample"] + f"; scaled to this run's work units (m={m}, "
+                         f"{len(range(k, m + 1, k))} PO steps, {cg_total} CG iterations)",
+               "per_unit_s": {kk: costs[kk] for kk in ("t_lanczos_iter", "t_po_row", "t_cg_iter")},
+               "value_kind": "extrapolated to this workload from the timed sample"}
+        if c1_res is not None:
+            cpu["measured_c1"] = c1_res
 
     if args.record_units and rank == 0:
         units_path = os.path.join(ROOT, "paper_0901_3512_gb300", "workload_units.json")
@@ -491,10 +602,14 @@ def run_ours(args):
                "e2e": e2e, "cpu_baseline": cpu}
         if fp64_cmp:
             out["fp64_plain"] = fp64_cmp
+        if cg_only_cmp:
+            out["cg_only"] = cg_only_cmp
         if classic_cmp is not None:
             out["classic_seeding"] = classic_cmp
         print(json.dumps(out))
     s.close()
+    if c1 is not None and cpu is None:
+        finish_oracle_c1(c1, 1.0)
     replicas.finish()
 
 
@@ -677,6 +792,9 @@ def run_deflate_eval(args):
 
 def main():
     args = _args()
+    if args.oracle_c1_worker:
+        oracle_c1_worker()
+        return
     if args.deflate_eval:
         run_deflate_eval(args)
         return

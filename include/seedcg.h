@@ -71,12 +71,16 @@ typedef struct {
                               iterated residual fell by this factor (default 0.1)      */
     int po_passes;         /* 1 = classical Gram-Schmidt, 2 = CGS2 (default 1)         */
     int seed_mode;         /* 0 = literal per-iteration updates (Algorithm 1 steps 3-7;
-                              FP64 only), 1 = blocked Eq. (1) after the Lanczos run,
+                              FP64 only), 1 = blocked: x^1 by the LU recurrence of steps
+                              3 and 6, the systems j >= 2 by Eq. (1) after the Lanczos run,
                               2 = classic repeated seeding, the comparison variant of
                               Section 1: each system in turn is run by Lanczos from its
                               current guess to convergence (past_factor and extra_iters
                               are not used) and seeds the systems after it by Eq. (1);
-                              CG then finishes any system still above tol              */
+                              CG then finishes any system still above tol;
+                              3 = no seeding: standard CG for every system from x_0
+                              (no Lanczos, no basis), the baseline Section 3 measures
+                              the seeded systems against; seedcg_solve only           */
     int x0_given;          /* 1: X holds initial guesses x_0^j on entry                */
     int cg_maxiter;        /* CG iteration cap per system (default 20000)               */
     int stop_after_seed;   /* 1: return the seeded guesses without running CG (tests)  */
@@ -211,7 +215,8 @@ seedcg_status seedcg_eo_reconstruct(seedcg_handle* h, int n, const double* x_odd
  * synchronisation of cudaMalloc / cudaFree on every call.  (The paper has no
  * counterpart: this is a property of the library, not of the method.)
  * Same arguments, layouts and results as seedcg_apply; in and out are the
- * caller's device buffers.  The scratch (internal copies of in, the
+ * caller's device buffers on the handle's GPU (host, pinned or unregistered
+ * memory is refused with SEEDCG_ERR_ARG before any kernel runs).  The scratch (internal copies of in, the
  * intermediate and the output) is one fixed 16 MiB device array that every
  * GPU loading this library holds until the process exits; the call returns
  * SEEDCG_ERR_ARG, with a message, when 3 * n * V * 12 * (16 B for prec 0,

@@ -332,8 +332,11 @@ def improved_seed_cg(M, B, X0, tol, m_max, reorth_period, past_factor=1.0, extra
     nrhs = B.shape[0]
     res = seed_lanczos(M, B, X0, tol, m_max, reorth_period, past_factor, extra_iters, po_passes)
     if seed_mode == "blocked":
+        # Eq. (1) is the closed form of steps 4 and 7 for the systems j >= 2; the
+        # first system's x^1 is the one steps 3 and 6 build by the LU recurrence
         X = galerkin_seed(res.V, res.alpha, res.beta, res.R0,
                           None if X0 is None else np.asarray(X0, dtype=np.complex128))
+        X[0] = res.X[0]
     else:
         X = res.X.copy()
     iters = np.zeros(nrhs, dtype=np.int64)
@@ -386,6 +389,7 @@ def classic_seed_cg(M, B, X0, tol, m_max, reorth_period=0, po_passes=1, seed_mod
         res = seed_lanczos(M, B[j:], start, tol, m_max, reorth_period, 1.0, 0, po_passes)
         if seed_mode == "blocked":
             X[j:] = galerkin_seed(res.V, res.alpha, res.beta, res.R0, start)
+            X[j] = res.X[0]      # the seed system's own x by steps 3 and 6
         else:
             X[j:] = res.X
         lz[j] = res.m

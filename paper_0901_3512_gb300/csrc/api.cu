@@ -42,7 +42,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.precision < 0 || o.precision > 2) { why = "unknown precision mode"; return false; }
     if (!(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)) { why = "reliable_delta must be in (0,1)"; return false; }
     if (o.po_passes < 1 || o.po_passes > 2) { why = "po_passes must be 1 or 2"; return false; }
-    if (o.seed_mode < 0 || o.seed_mode > 2) { why = "seed_mode must be 0, 1 or 2"; return false; }
+    if (o.seed_mode < 0 || o.seed_mode > 3) { why = "seed_mode must be 0, 1, 2 or 3"; return false; }
     if (o.seed_mode == 0 && o.precision != SEEDCG_FP64) { why = "literal seeding (seed_mode 0) needs precision FP64"; return false; }
     if (o.cg_maxiter < 1) { why = "cg_maxiter must be >= 1"; return false; }
     if (o.poll_every < 1) { why = "poll_every must be >= 1"; return false; }
@@ -196,6 +196,8 @@ seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrh
             return fail(h0, SEEDCG_ERR_ARG, "batch: all handles need the same precision and device");
         if (hs[f]->opt.resid_mode != 0)
             return fail(h0, SEEDCG_ERR_ARG, "batch: resid_mode = 1 is supported by seedcg_solve only");
+        if (hs[f]->opt.seed_mode > 1)
+            return fail(h0, SEEDCG_ERR_ARG, "batch: seed_mode 2 and 3 are supported by seedcg_solve only");
         for (int g = 0; g < f; g++)
             if (hs[g] == hs[f]) return fail(h0, SEEDCG_ERR_ARG, "batch: a handle appears twice");
         total += nrhs[f];

@@ -196,20 +196,29 @@ k_lz_eta(const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ r0, long n, 
 }
 
 // Steps 5-7 vector part: f -= alpha_i v_i; beta_i = ||f|| (final unless PO
-// follows).  Literal mode also: w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i,
-// x^1 += zeta_i w_i, x^j += eta^j w_i.
-template <typename R, bool LIT>
+// follows).  MODE selects the solution updates of steps 3 and 6-7 done in the
+// same pass:
+//   LZ_LITERAL  w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i, x^1 += zeta_i w_i,
+//               x^j += eta^j w_i, all in R (the literal seeding of FP64 runs);
+//   LZ_X1       w_i in R and x^1 += zeta_i w_i accumulated in FP64 (x1 = the
+//               FP64 solution of RHS 1; the systems j >= 2 take Eq. (1) later).
+enum { LZ_PLAIN = 0, LZ_LITERAL = 1, LZ_X1 = 2 };
+template <typename R, int MODE>
 __global__ void __launch_bounds__(kRedThreads)
 k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __restrict__ w,
-            cx_t<R>* __restrict__ X, int nrhs, long n, int i, int final_beta, LzDev L) {
+            cx_t<R>* __restrict__ X, double2* __restrict__ x1, int nrhs, long n, int i,
+            int final_beta, LzDev L) {
+    constexpr bool LIT = MODE == LZ_LITERAL;
     if (i > L.ctl->m) return;
     const R a = (R)L.alpha[i - 1];
-    R dl = 0, bp = 0, zt = 0;
-    if (LIT) {
+    R dl = 0, bp = 0, zt = 0, idl = 0;
+    if (MODE != LZ_PLAIN) {
         dl = (R)L.delta[i - 1];
         bp = i > 1 ? (R)L.beta[i - 2] : R(0);
         zt = (R)L.zeta[i - 1];
+        idl = (R)(1.0 / L.delta[i - 1]);
     }
+    const double zt64 = MODE == LZ_X1 ? L.zeta[i - 1] : 0.0;
     R part = 0;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
          e += (long)gridDim.x * blockDim.x) {
@@ -218,6 +227,16 @@ k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __r
         fv.y -= a * vv.y;
         f[e] = fv;
         part += fv.x * fv.x + fv.y * fv.y;
+        if (MODE == LZ_X1) {
+            cx_t<R> ww = i > 1 ? w[e] : mk<R>(0, 0);
+            ww.x = (vv.x - bp * ww.x) * idl;
+            ww.y = (vv.y - bp * ww.y) * idl;
+            w[e] = ww;
+            double2 xv = x1[e];
+            xv.x = fma(zt64, (double)ww.x, xv.x);
+            xv.y = fma(zt64, (double)ww.y, xv.y);
+            x1[e] = xv;
+        }
         if (LIT) {
             cx_t<R> ww = i > 1 ? w[e] : mk<R>(0, 0);
             ww.x = (vv.x - bp * ww.x) / dl;
@@ -767,11 +786,11 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
             }
             const bool po_now = k_po > 0 && i >= 2 && (i % k_po) == 0;
             if (literal)
-                k_lz_update<R, true><<<rb, kRedThreads, 0, st>>>(v, fv, wv, reinterpret_cast<cx_t<R>*>(X64),
-                                                               nrhs, n, i, po_now ? 0 : 1, L);
+                k_lz_update<R, LZ_LITERAL><<<rb, kRedThreads, 0, st>>>(
+                    v, fv, wv, reinterpret_cast<cx_t<R>*>(X64), nullptr, nrhs, n, i, po_now ? 0 : 1, L);
             else
-                k_lz_update<R, false><<<rb, kRedThreads, 0, st>>>(v, fv, wv, nullptr, nrhs, n, i,
-                                                                po_now ? 0 : 1, L);
+                k_lz_update<R, LZ_X1><<<rb, kRedThreads, 0, st>>>(v, fv, wv, nullptr, X64, nrhs, n, i,
+                                                                 po_now ? 0 : 1, L);
             SEEDCG_CHECK_LAUNCH();
             if (po_now) {
                 cudaEvent_t e0, e1;
@@ -833,11 +852,13 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
 
     // ---------------- phase S: Galerkin seeds, Eq. (1) ----------------
     t_seed.start(st);
-    if (!literal && m > 0) {
-        project(m, R0, nrhs, nrhs);
-        k_seed_tridiag<<<(nrhs + 63) / 64, 64, 0, st>>>(Cc, nrhs, nrhs, m, L);
+    // x^1 already holds steps 3 and 6 (the LU recurrence); Eq. (1) seeds j >= 2
+    const int ns = nrhs - 1;
+    if (!literal && m > 0 && ns > 0) {
+        project(m, R0 + n, ns, ns);
+        k_seed_tridiag<<<(ns + 63) / 64, 64, 0, st>>>(Cc, ns, ns, m, L);
         SEEDCG_CHECK_LAUNCH();
-        gemm_n<R, VT, double2>(Vb, n, m, Cc, nrhs, nrhs, X64, n, n, 1.0, st);
+        gemm_n<R, VT, double2>(Vb, n, m, Cc, ns, ns, X64 + n, n, n, 1.0, st);
     }
     t_seed.stop(st);
 
@@ -1261,6 +1282,50 @@ seedcg_status classic_rounds(seedcg_handle* h, int nrhs, double2* B64, double2* 
     return code;
 }
 
+// No seeding (seed_mode 3): standard CG for every system from its x_0, all of
+// them in the batched engine.  Section 3 measures the seeded systems against
+// this baseline (standard CG from zero); it runs no Lanczos and stores no basis.
+template <typename R>
+seedcg_status cg_only(seedcg_handle* h, int nrhs, double2* B64, double2* X64, double tol,
+                      seedcg_info* info, cudaStream_t st) {
+    const seedcg_options& o = h->opt;
+    const bool x0 = o.x0_given || h->force_x0;
+    CgResult cgr;
+    PhaseTimer t_cg;
+    t_cg.start(st);
+    std::vector<CgGroup> gs{{h, nrhs, B64, X64}};
+    const int poll = o.poll_every > 0 ? o.poll_every : 32;
+    batched_cg<R>(gs, tol, sizeof(R) == 8 ? 0.0 : o.reliable_delta, o.cg_maxiter, poll, true, h->cgbuf,
+                  h->pinned, cgr, st);
+    t_cg.stop(st);
+    h->last_m = 0;
+    h->vbasis_m = 0;
+    h->alpha.clear();
+    h->beta.clear();
+    h->delta.clear();
+    seedcg_status code = SEEDCG_OK;
+    for (int j = 0; j < nrhs; j++)
+        if (cgr.notconv[0][j] || !(cgr.true_resid[0][j] <= tol)) code = SEEDCG_ERR_NOT_CONVERGED;
+    if (info) {
+        info->m_conv = 0;
+        info->m = 0;
+        info->po_count = 0;
+        int mx = 0;
+        for (int j = 0; j < nrhs; j++) mx = std::max(mx, cgr.iters[0][j]);
+        info->cg_iters_max = mx;
+        info->reliable_updates = cgr.reliable_updates;
+        for (int j = 0; j < nrhs; j++) {
+            if (info->iters) info->iters[j] = cgr.iters[0][j];
+            if (info->matvecs) info->matvecs[j] = 2 * (cgr.iters[0][j] + cgr.ru[0][j]) + (x0 ? 2 : 0);
+            if (info->true_resid) info->true_resid[j] = cgr.true_resid[0][j];
+        }
+        info->ms_lanczos = info->ms_po = info->ms_seed = 0.f;
+        info->ms_cg = t_cg.read();
+        info->ms_total = info->ms_cg;
+    }
+    return code;
+}
+
 // ratio[j] = ||eta_j - D x_j|| / ||eta_j|| in FP64 (T: scratch of nrhs fields)
 void d_residuals(seedcg_handle* h, int nrhs, const double2* E64, const double2* X64, double2* T64,
                  std::vector<double>& ratio, cudaStream_t st) {
@@ -1403,7 +1468,10 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
         h->force_x0 = true;
     }
     seedcg_status code;
-    if (h->opt.seed_mode == 2) {
+    if (h->opt.seed_mode == 3) {
+        code = h->opt.precision == SEEDCG_FP64 ? cg_only<double>(h, nrhs, B64, X64, tol, info, st)
+                                                : cg_only<float>(h, nrhs, B64, X64, tol, info, st);
+    } else if (h->opt.seed_mode == 2) {
         switch (h->opt.precision) {
             case SEEDCG_FP64:
                 code = classic_rounds<double, double2>(h, nrhs, B64, X64, tol, reorth_period, info, st);

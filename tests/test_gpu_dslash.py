@@ -35,6 +35,8 @@ def test_dslash_parity(dims, kappa, n, multi):
         s.apply(code, xd, out, prec=1, multi=multi)
         got32 = host(out)
         assert rel(got32, want) <= 1e-5, (code, rel(got32, want))
+        # element by element: no entry off by more than the FP32 bar of the largest
+        assert np.abs(got32 - want).max() <= 1e-5 * np.abs(want).max(), code
     s.close()
 
 

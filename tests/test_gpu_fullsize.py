@@ -1,0 +1,150 @@
+"""Parity at the size and in the launch configuration the benchmark times:
+the 16^3x32 lattice (eps 0.5, seed 2, kappa tuned to cond(M) ~ 1e5), twelve
+unit point sources, mixed precision with the stored basis V in bf16 and the
+Eq. (1) seed projection on tcgen05 tensor cores, PO every k = 10 iterations,
+RHS 1 run 2x past convergence, m_max 8000 (Section 2, Algorithm 1 + Eq. 1;
+Section 3's setting of one gauge field with many right-hand sides).
+
+What is checked, all against the oracle or against mathematics:
+  * every solution's residual ||b - M x|| / ||b|| recomputed with the
+    oracle's plain-C FP64 operator (b = D^dag eta also from the oracle) meets
+    tol, up to the rounding of an FP64 recomputation in another summation
+    order (<= 100 eps ||M|| ||x|| / ||b||);
+  * the distance to a plain FP64 GPU solve of the same systems is within
+    the bound that two residuals <= tol allow: ||x - x'|| / ||x'|| <=
+    2 cond(M) (r + r'), cond from the tuned field's extreme Ritz values;
+  * the tcgen05 projection V^dag X over the whole stored basis (N = 1.57 M
+    complex entries per row, > 2000 rows) equals the FP64 product of the
+    same stored rows with the same vectors, element by element, on sampled
+    rows (first and last rows, tile edges, random rows), within the bf16
+    rounding bound 2^-9 ||v_a|| ||x_j|| of the operand plus FP32 sums.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.wilson import WilsonOperator
+from paper_0901_3512_gb300 import seedcg, workloads as W
+from tests.gpu_helpers import dev, host, need_gpu, recompute_slack, rel
+
+pytestmark = pytest.mark.gpu
+
+WL = "large_16x16x16x32_nrhs12"
+M_MAX = 8000          # the benchmark's m_max (it sizes the basis and the TMA tensor map)
+
+
+_recompute_bound = recompute_slack
+
+
+@pytest.fixture(scope="module")
+def headline():
+    need_gpu()
+    import torch
+    wl = W.WORKLOADS[WL]
+    f = wl.fields[0]
+    tab = W.kappa_table()[f.name]
+    kappa = tab["kappa"]
+    u = f.gauge()
+    op = WilsonOperator(f.dims, u, kappa)
+    eta = wl.sources_for(0)
+    B = np.stack([op.Ddag(e) for e in eta])            # the oracle's right-hand sides
+    s = seedcg.Solver(f.dims, u, kappa, precision="mixed_vbf16", past_factor=wl.past_factor,
+                      m_max=M_MAX, use_tensor_cores=1)
+    Bd = dev(B)
+    X = dev(np.zeros_like(B))
+    code, info = s.solve(Bd, X, wl.tol, 0, wl.reorth_period)
+    out = {"wl": wl, "f": f, "tab": tab, "op": op, "B": B, "code": code, "info": info,
+           "X": host(X), "solver": s}
+    yield out
+    s.close()
+    torch.cuda.empty_cache()
+
+
+def test_headline_solutions_meet_tol_by_the_oracle(headline):
+    h = headline
+    assert h["code"] == seedcg.SEEDCG_OK
+    op, B, X, tol = h["op"], h["B"], h["X"], h["wl"].tol
+    lam_max = h["tab"]["lam_max"]
+    worst = 0.0
+    for j in range(B.shape[0]):
+        b = B[j].reshape(-1)
+        x = X[j].reshape(-1)
+        rd = np.linalg.norm(b - op.M(x)) / np.linalg.norm(b)
+        slack = _recompute_bound(lam_max, np.linalg.norm(x), np.linalg.norm(b))
+        assert rd <= tol + slack, (j, rd, slack)
+        # the library's own FP64 residual agrees with the oracle's recomputation
+        assert abs(h["info"]["true_resid"][j] - rd) <= slack + 1e-3 * rd, (j, rd, h["info"]["true_resid"][j])
+        worst = max(worst, rd)
+    info = h["info"]
+    print(f"16^3x32 bf16: m_conv {info['m_conv']} m {info['m']} PO {info['po_count']} "
+          f"iters {info['iters']} worst oracle residual {worst:.3e}")
+
+
+def test_headline_tc_projection_full_basis_matches_fp64(headline):
+    """seedcg_project_basis over every stored row on tcgen05, sampled rows
+    compared with the FP64 product of the widened stored rows."""
+    import torch
+    h = headline
+    s, f = h["solver"], h["f"]
+    m = h["info"]["m"]
+    assert m >= 2000
+    vol = W.volume(f.dims)
+    nvec = 12
+    xs = W.random_spinors(f.dims, nvec, 77)
+    c_tc = seedcg.seedcg_project_basis(s.h, m, nvec, dev(xs), use_tensor_cores=1)
+    assert c_tc.shape == (m, nvec) and np.all(np.isfinite(c_tc))
+    rng = np.random.default_rng(5)
+    rows = sorted(set([0, 1, 2, 127, 128, 129, 255, 256, 511, 512, 1023, 1024, 2047, m - 129,
+                       m - 128, m - 2, m - 1] + list(rng.integers(0, m, 40))))
+    xf = xs.reshape(nvec, -1)
+    xn = np.linalg.norm(xf, axis=1)
+    buf = torch.zeros((1, vol, 4, 3), dtype=torch.complex128, device="cuda")
+    worst = 0.0
+    for a in rows:
+        seedcg.seedcg_get_basis(s.h, int(a), 1, buf)
+        va = host(buf).reshape(-1)
+        exact = va.conj() @ xf.T
+        bound = (2.0 ** -9 + 2e-6) * np.linalg.norm(va) * xn
+        err = np.abs(c_tc[a] - exact)
+        assert np.all(err <= bound), (a, err.max(), bound.min())
+        worst = max(worst, float((err / bound).max()))
+    print(f"tcgen05 projection over {m} rows: worst error / bound on {len(rows)} sampled rows = {worst:.3f}")
+
+
+def test_headline_matches_plain_fp64_gpu_solve(headline):
+    """The same systems solved in plain FP64 on the GPU (itself held to the
+    oracle's solutions and iteration counts on the 4^4 and 8^3x16 workloads):
+    both meet tol by the oracle, and the solutions lie within the distance two
+    residuals <= tol allow."""
+    import torch
+    h = headline
+    wl, f, op, B = h["wl"], h["f"], h["op"], h["B"]
+    # free the bf16 solve's basis before the FP64 one (about 100 GB)
+    X_mixed = h["X"]
+    info_mixed = h["info"]
+    h["solver"].close()
+    torch.cuda.empty_cache()
+    s64 = seedcg.Solver(f.dims, f.gauge(), h["tab"]["kappa"], precision="fp64",
+                        past_factor=wl.past_factor, m_max=5000)
+    X = dev(np.zeros_like(B))
+    code, info = s64.solve(dev(B), X, wl.tol, 0, wl.reorth_period)
+    s64.close()
+    torch.cuda.empty_cache()
+    assert code == seedcg.SEEDCG_OK
+    X64 = host(X)
+    cond = h["tab"]["cond"]
+    lam_max = h["tab"]["lam_max"]
+    for j in range(B.shape[0]):
+        b = B[j].reshape(-1)
+        x64 = X64[j].reshape(-1)
+        r64 = np.linalg.norm(b - op.M(x64)) / np.linalg.norm(b)
+        rm = np.linalg.norm(b - op.M(X_mixed[j].reshape(-1))) / np.linalg.norm(b)
+        slack = _recompute_bound(lam_max, np.linalg.norm(x64), np.linalg.norm(b))
+        assert r64 <= wl.tol + slack
+        d = rel(X_mixed[j], x64)
+        assert d <= 2 * cond * (r64 + rm), (j, d, r64, rm)
+    # the mixed run's Krylov dimension at convergence is the FP64 run's, up to
+    # the rounding of the bf16 basis and FP32 vectors (reported, loosely held)
+    assert abs(info_mixed["m_conv"] - info["m_conv"]) <= math.ceil(0.1 * info["m_conv"])
+    print(f"m_conv mixed {info_mixed['m_conv']} FP64 {info['m_conv']}; FP64 iters {info['iters']}")

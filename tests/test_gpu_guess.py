@@ -32,6 +32,7 @@ def test_forward_matches_oracle():
     for k in range(3):
         want, _ = net.forward(Ws, B[k])
         assert rel(got[k], want) <= 1e-5
+        assert np.abs(got[k] - want).max() <= 1e-5 * np.abs(want).max()
     # weights round-trip
     w = seedcg.seedcg_guess_get_weights(s.h)
     assert np.allclose(w, np.concatenate([x.reshape(-1) for x in Ws]), rtol=1e-6, atol=1e-7)
@@ -51,6 +52,7 @@ def test_loss_and_gradient_match_oracle():
     gw = seedcg.split_weights(g)
     for layer in range(3):
         assert rel(gw[layer], gref[layer]) <= 1e-4, layer
+        assert np.abs(gw[layer] - gref[layer]).max() <= 1e-4 * np.abs(gref[layer]).max(), layer
     s.close()
 
 
