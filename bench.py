@@ -71,6 +71,8 @@ def _args():
                         "period (k), first-RHS cost against k; 'kappa' scans --kappas. One JSON "
                         "line per setting (not a bench line)")
     p.add_argument("--kappa", type=float, default=None, help="with --sweep: kappa of the field")
+    p.add_argument("--po-passes", type=int, default=1, choices=[1, 2],
+                   help="with --sweep: Gram-Schmidt passes per PO step (2 = CGS2)")
     p.add_argument("--kappas", default="", help="with --sweep kappa: comma-separated values")
     p.add_argument("--guess-eval", action="store_true",
                    help="learned initial guess on the workload's field: train on (b, x) pairs the "
@@ -84,6 +86,10 @@ def _args():
     p.add_argument("--eval-pairs", type=int, default=64)
     p.add_argument("--epochs", type=int, default=10)
     p.add_argument("--lr", type=float, default=3e-3)
+    p.add_argument("--eo", action="store_true",
+                   help="the even-odd preconditioned system of Section 3 (A^dag A x_o = A^dag phi on "
+                        "odd-site half vectors) on the same workload: its own JSON line with its PO "
+                        "roofline, beside one full-lattice solve of the same sources (not a bench line)")
     p.add_argument("--only", default=None, choices=["dslash", "po"],
                    help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
                         "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
@@ -613,6 +619,84 @@ def run_ours(args):
     replicas.finish()
 
 
+def run_eo(args):
+    """Section 3's even-odd system on the workload: time-to-solution of seedcg_solve_eo for all
+    right-hand sides (binding residual of A^dag A x_o = b, the original system's residual
+    reported), the PO roofline on half-length rows, and one full-lattice solve beside it."""
+    import numpy as np
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[args.workload]
+    f = wl.fields[0]
+    prec = args.precision or wl.precision
+    kappa = W.kappa_for(f.name)
+    gauge = f.gauge()
+    k = wl.reorth_period
+    s = seedcg.Solver(f.dims, gauge, kappa, precision=prec, past_factor=wl.past_factor, m_max=args.m_max)
+    eta = torch.from_numpy(wl.sources_for(0)).cuda()
+    X = torch.zeros_like(eta)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        seedcg.seedcg_solve_eo(s.h, eta, X, wl.tol, 0, k, stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = seedcg.seedcg_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        code, info = seedcg.seedcg_solve_eo(s.h, eta, X, wl.tol, 0, k, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = seedcg.seedcg_kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks, peak_kind = _peaks()
+    vol = int(np.prod(f.dims))
+    n = 12 * vol // 2
+    vbytes = {"fp64": 16, "mixed_v32": 8, "mixed_vbf16": 4}[prec]
+    m = info["m"]
+    po_rows = sum(i - 1 for i in range(k, m + 1, k)) if k else 0
+    po_alg = 2 * po_rows * n * vbytes
+    po_gbs = po_alg / (info["ms_po"] / 1000.0) / 1e9 if info["ms_po"] > 0 else None
+    # the same sources on the full lattice, for comparison
+    B = torch.empty_like(eta)
+    s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+    Xf = torch.zeros_like(B)
+    s.solve(B, Xf, wl.tol, 0, k, stream=stream)
+    Xf.zero_()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    cf, inf_full = s.solve(B, Xf, wl.tol, 0, k, stream=stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    full_s = ea.elapsed_time(eb) / 1000.0
+    out = {"mode": "even_odd", "metric": METRIC, "value": ms / 1000.0, "unit": "s", "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "dtype": {"fp64": "f64", "mixed_v32": "f32+c64V+f64", "mixed_vbf16": "f32+bf16V+f64"}[prec],
+           "data": "synthetic", "config": dict(_config(args, wl, 1), system="A^dag A x_o = A^dag phi (odd sites)"),
+           "valid": code == 0 and max(info["true_resid"]) <= wl.tol,
+           "solve": {"m_conv": info["m_conv"], "m": m, "po_count": info["po_count"],
+                     "cg_iters_max": info["cg_iters_max"], "iters": info["iters"],
+                     "max_true_resid": max(info["true_resid"]),
+                     "max_true_resid_D": max(info["true_resid_D"]),
+                     "ms_lanczos": info["ms_lanczos"], "ms_po": info["ms_po"], "ms_seed": info["ms_seed"],
+                     "ms_cg": info["ms_cg"]},
+           "roofline": {"bound": "hbm", "achieved": po_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": po_gbs / peaks["hbm_gbs"] if po_gbs else None, "traffic": None,
+                        "kernel": "periodic re-orthogonalisation against the half-length basis",
+                        "peak_kind": peak_kind, "algorithmic_bytes_per_solve": po_alg,
+                        "ms_per_solve": info["ms_po"]},
+           "full_lattice": {"seconds": full_s, "status": cf, "m_conv": inf_full["m_conv"], "m": inf_full["m"],
+                            "ms_po": inf_full["ms_po"], "ms_cg": inf_full["ms_cg"],
+                            "cg_iters_max": inf_full["cg_iters_max"],
+                            "po_bytes_per_solve": 2 * sum(i - 1 for i in range(k, inf_full["m"] + 1, k)) * 2 * n * vbytes,
+                            "speedup_eo_over_full": full_s / (ms / 1000.0)},
+           "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(out))
+    s.close()
+
+
 def run_only(args):
     """Small runs of single kernels for ncu captures (not bench lines)."""
     import torch
@@ -651,7 +735,8 @@ def run_sweep(args):
     eta_all = W.point_sources(f.dims, 2)
 
     def run(kappa, pf, k, nrhs=2):
-        s = seedcg.Solver(f.dims, gauge, kappa, precision=prec, past_factor=pf, m_max=args.m_max)
+        s = seedcg.Solver(f.dims, gauge, kappa, precision=prec, past_factor=pf, m_max=args.m_max,
+                          po_passes=args.po_passes)
         eta = torch.from_numpy(eta_all[2 - nrhs:]).cuda()
         B = torch.empty_like(eta)
         s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
@@ -678,6 +763,7 @@ def run_sweep(args):
     kappa = args.kappa if args.kappa is not None else W.kappa_for(f.name)
     cg0 = plain_cg(kappa)
     base = {"workload": args.workload, "lattice": list(f.dims), "kappa": kappa, "precision": prec,
+            "po_passes": args.po_passes,
             "tol": wl.tol, "plain_cg_iters_rhs2": cg0, "plain_cg_matvecs_rhs2": 2 * cg0}
     settings = ([(pf, 10) for pf in (1.0, 1.2, 1.4, 1.6, 2.0)] if args.sweep == "m"
                 else [(1.4, k) for k in (10, 100, 200, 250, 0)])
@@ -806,6 +892,9 @@ def main():
         return
     if args.only:
         run_only(args)
+        return
+    if args.eo:
+        run_eo(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -194,12 +194,18 @@ seedcg_status seedcg_apply_eo(seedcg_handle* h, int op, int prec, int n, const d
 seedcg_status seedcg_eo_source(seedcg_handle* h, int n, const double* eta, double* phi, void* stream);
 /*
  * Improved Seed-CG on the even-odd system (Section 3 solves A^dag A x_o = A^dag phi):
- * for each right-hand side eta (device, full [nrhs][V][4][3]) phi = eta_o + kappa H_oe eta_e,
- * Algorithm 1 on A^dag A with the handle's options (FP64 only: precision and seed_mode are
- * not used; blocked Eq. (1) seeds), CG for every system above tol, and the full solution x
- * (device, full) by x_e = eta_e + kappa H_eo x_o.  The criterion is ||b - A^dag A x_o|| <= tol ||b||,
- * b = A^dag phi, reported in info->true_resid.  Host-driven: scalars on the host, vectors in
- * this library's kernels.
+ * for each right-hand side eta (device, full [nrhs][V][4][3]) phi = eta_o + kappa H_oe eta_e
+ * and b = A^dag phi are formed in FP64, Algorithm 1 runs on A^dag A with the handle's
+ * options on the device-resident engine of seedcg_solve (every precision mode and seeding
+ * form seed_mode 0-3: Lanczos with the LU of T, PO, Eq. (1) seeds, the batched CG with FP64
+ * reliable updates), on odd-site half vectors; then x_e = eta_e + kappa H_eo x_o gives the
+ * full solution x (device, full; on entry x_0 if opt.x0_given, of which the odd sites are
+ * used).  The binding criterion is ||b - A^dag A x_o|| <= tol ||b|| in FP64
+ * (info->true_resid); info->true_resid_D, when not NULL, receives the original system's
+ * ||eta - D x|| / ||eta|| in FP64.  info->matvecs counts applications of the full-lattice
+ * D: one A^dag A (four half-lattice hops) counts 2.  use_guess and resid_mode = 1 are
+ * refused (SEEDCG_ERR_ARG).  Afterwards seedcg_get_basis returns odd-site half vectors
+ * [count][V/2][4][3]; seedcg_project_basis and seedcg_deflate_guess refuse the basis.
  */
 seedcg_status seedcg_solve_eo(seedcg_handle* h, int nrhs, const double* eta, double* x, double tol,
                               int extra_iters, int reorth_period, seedcg_info* info, void* stream);

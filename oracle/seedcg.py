@@ -161,7 +161,12 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
         # orthogonality beyond repair between two PO steps, or the Krylov space
         # is exhausted).  Reading: the run ends at i - 1 when a projection
         # pass leaves ||v_i|| < 1/2, or when re-orthogonalising lengthens f
-        # (an orthogonal projection never does); the systems then go to CG.
+        # by more than 1 %; the systems then go to CG.  Both follow from
+        # ||v - V c||^2 = ||v||^2 - ||c||^2 + c^dag (V^dag V - I) c, c = V^dag v:
+        # with an orthonormal V a pass never lengthens a vector (growth beyond
+        # rounding means V^dag V has an eigenvalue above 2, a direction stored
+        # more than once), and ||v'|| < 1/2 means v_i lies within 30 degrees
+        # of the stored space, an order-one loss of orthogonality.
         if reorth_period > 0 and i % reorth_period == 0:
             beta_pre = _norm(f)
             v_po, f_po, ok = periodic_reorth(V, i, v, f, po_passes, guard=True)

@@ -319,7 +319,8 @@ seedcg_status seedcg_get_basis(seedcg_handle* h, int first, int count, double* o
         return fail(h, SEEDCG_ERR_ARG, "requested rows are outside the stored basis");
     if (count == 0) return SEEDCG_OK;
     try {
-        const int vol = h->g.vol;
+        // rows of an even-odd solve are odd-site half vectors
+        const int vol = h->vbasis_eo ? h->g.vol / 2 : h->g.vol;
         const long n = 12L * vol;
         const size_t bytes = (size_t)count * n * sizeof(double2);
         seedcg::DevBuf wide, canon;
@@ -362,6 +363,7 @@ seedcg_status seedcg_deflate_guess(seedcg_handle* h, int nev, int nr, const doub
                                    double* ritz_values, void* stream) {
     if (!h || !B || !X0) return fail(h, SEEDCG_ERR_ARG, "h, B or X0 is NULL");
     if (h->vbasis_m < 1) return fail(h, SEEDCG_ERR_ARG, "no stored basis: run seedcg_solve first");
+    if (h->vbasis_eo) return fail(h, SEEDCG_ERR_ARG, "the stored basis is of the even-odd system (half vectors)");
     if (nev < 1 || nev > 64 || nev > h->vbasis_m || nr < 1 || nr > 256)
         return fail(h, SEEDCG_ERR_ARG, "nev must be in [1, min(64, basis size)], nr in [1, 256]");
     if (!is_device_ptr(B) || !is_device_ptr(X0)) return fail(h, SEEDCG_ERR_ARG, "B and X0 must be device pointers");
@@ -383,6 +385,7 @@ seedcg_status seedcg_project_basis(seedcg_handle* h, int rows, int nvec, const d
     if (rows < 1 || rows > h->vbasis_m || nvec < 1 || nvec > 32)
         return fail(h, SEEDCG_ERR_ARG, "rows must be in [1, stored basis size], nvec in [1, 32]");
     if (!is_device_ptr(X)) return fail(h, SEEDCG_ERR_ARG, "X must be a device pointer");
+    if (h->vbasis_eo) return fail(h, SEEDCG_ERR_ARG, "the stored basis is of the even-odd system (half vectors)");
     try {
         SEEDCG_CUDA_TRY(cudaSetDevice(h->device));
         seedcg_status c = seedcg::project_basis_impl(h, rows, nvec, X, C, use_tensor_cores ? 1 : 0,

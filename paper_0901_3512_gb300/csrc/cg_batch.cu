@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "cg_batch.cuh"
+#include "eo.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 #include "wilson.cuh"
@@ -43,7 +44,9 @@ struct GroupDev {
     Geom g;
     const cx_t<R>* u;   // links in the working precision
     R kappa;
-    long n;             // 12 * volume
+    long n;             // 12 * sites (the volume, or half of it for the even-odd system)
+    int eo;             // 1: M = A^dag A on odd-site half vectors (Section 3's system)
+    cx_t<R>* e;         // [cap][n] even-site intermediate of the even-odd operator
     cx_t<R>* xr;        // [cap][n] iterate increments since the last reliable update
     cx_t<R>* r;
     cx_t<R>* p;
@@ -160,6 +163,61 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
         }
         if (DOT) {
             // lanes in the working precision, tiles in FP64 (k_mf_alpha)
+            const double d = (double)warp_sum_t(dr);
+            if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
+        }
+    }
+}
+
+// 1-2 for the even-odd system: M p = A^dag A p in four parity-restricted hops over
+// every active system of every field (tiles of TS odd / even half sites):
+//   STAGE 0  e = H_eo p;  1  t = p - kappa^2 H_oe e;  2  e = H^dag_eo t;
+//   STAGE 3  q = t - kappa^2 H^dag_oe e, with the tile shares of Re p^dag q
+template <typename R, int STAGE, int RPB>
+__global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? 2 : 1))
+k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
+    constexpr int DAG = STAGE >= 2 ? 1 : 0;
+    constexpr int POUT = (STAGE & 1) ? 1 : 0;
+    constexpr bool DOT = STAGE == 3;
+    __shared__ int s_tile0[kMaxGroups];
+    if (threadIdx.x < ng) s_tile0[threadIdx.x] = G[threadIdx.x].tile0;
+    __syncthreads();
+    const int f = find_group(blockIdx.x, ng, s_tile0);
+    const GroupDev<R>& gd = G[f];
+    const int nsys = rows.nact[f];
+    if (nsys == 0) return;
+    const Geom g = gd.g;
+    const int vh = g.vol / 2;
+    const int tile = blockIdx.x - gd.tile0;
+    const int j = threadIdx.x % TS;
+    const int qg = threadIdx.x / TS;
+    const int hh = tile * TS + j;
+    const bool live = hh < vh;
+    const R kk = gd.kappa * gd.kappa;
+    const cx_t<R>* in = STAGE == 0 ? gd.p : STAGE == 2 ? gd.t : gd.e;
+    const cx_t<R>* same = STAGE == 1 ? gd.p : STAGE == 3 ? gd.t : nullptr;
+    cx_t<R>* out = (STAGE == 0 || STAGE == 2) ? gd.e : STAGE == 1 ? gd.t : gd.q;
+    for (int r = qg; r < nsys; r += RPB) {
+        R dr = 0;
+        if (live) {
+            const size_t off = (size_t)r * gd.n;
+            Spinor<R> acc;
+            eo_site_apply<R, DAG>(g, gd.u, POUT, hh, in + off, POUT ? same + off : nullptr, R(1),
+                                  POUT ? -kk : R(1), acc);
+            store_spinor(out + off, vh, hh, acc);
+            if (DOT) {
+                const cx_t<R>* pr = gd.p + off;
+                R acc2 = 0;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    const cx_t<R> pz = __ldg(pr + sidx(k, hh, vh));
+                    const cx_t<R> rz = acc.c[k / 3][k % 3];
+                    acc2 += pz.x * rz.x + pz.y * rz.y;
+                }
+                dr = acc2;
+            }
+        }
+        if (DOT) {
             const double d = (double)warp_sum_t(dr);
             if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
         }
@@ -365,8 +423,36 @@ void launch_mf(int rpb, int dag, int tiles, cudaStream_t s, const GroupDev<R>* g
     SEEDCG_CHECK_LAUNCH();
 }
 
+template <typename R>
+void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+#define SEEDCG_MFE(RP)                                                                          \
+    switch (stage) {                                                                           \
+        case 0: k_mf_eo<R, 0, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
+        case 1: k_mf_eo<R, 1, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
+        case 2: k_mf_eo<R, 2, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
+        default: k_mf_eo<R, 3, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;           \
+    }
+    if (rpb == 4) { SEEDCG_MFE(4) }
+    else if (rpb == 12) { SEEDCG_MFE(12) }
+    else { SEEDCG_MFE(8) }
+#undef SEEDCG_MFE
+    SEEDCG_CHECK_LAUNCH();
+}
+
+// q = M p for every active system: 2 launches (D, D^dag) or 4 (even-odd hops)
+template <typename R>
+void launch_op(bool eo, int rpb, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+    if (eo) {
+        for (int stage = 0; stage < 4; stage++) launch_mf_eo<R>(rpb, stage, tiles, s, gdev, ng, rows);
+    } else {
+        launch_mf<R>(rpb, 0, tiles, s, gdev, ng, rows);
+        launch_mf<R>(rpb, 1, tiles, s, gdev, ng, rows);
+    }
+}
+
 std::string tune_key(const std::vector<CgGroup>& groups, bool fp64) {
     std::string k = fp64 ? "mf_dslash f64" : "mf_dslash f32";
+    if (!groups.empty() && groups[0].h->eo_active) k += " eo";
     for (auto& g : groups) {
         char b[96];
         snprintf(b, sizeof(b), " %dx%dx%dx%d:%d", g.h->g.L[0], g.h->g.L[1], g.h->g.L[2], g.h->g.L[3], g.nsys);
@@ -424,13 +510,11 @@ int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const GroupDev<R
     SEEDCG_CUDA_TRY(cudaEventCreate(&b));
     int best = 8;
     float best_ms = 1e30f;
+    const bool eo = groups[0].h->eo_active;
     for (int c : cands) {
-        launch_mf<R>(c, 0, tiles, st, gdev, ng, rows);  // warm-up
+        launch_op<R>(eo, c, tiles, st, gdev, ng, rows);  // warm-up
         SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
-        for (int r = 0; r < 3; r++) {
-            launch_mf<R>(c, 0, tiles, st, gdev, ng, rows);
-            launch_mf<R>(c, 1, tiles, st, gdev, ng, rows);
-        }
+        for (int r = 0; r < 3; r++) launch_op<R>(eo, c, tiles, st, gdev, ng, rows);
         SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -475,13 +559,18 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     if (ng < 1 || ng > kMaxGroups) throw Error{SEEDCG_ERR_ARG, "1..16 gauge fields per batch"};
     const bool fp64 = sizeof(R) == 8;
     const size_t cxR = sizeof(cx_t<R>);
+    const bool eo = groups[0].h->eo_active;
+    for (auto& gr : groups)
+        if (gr.h->eo_active != eo) throw Error{SEEDCG_ERR_ARG, "a batch mixes even-odd and full systems"};
+    // sites of a system's vectors: the lattice, or its odd half for the even-odd system
+    auto nsites = [&](const CgGroup& gr) { return eo ? gr.h->g.vol / 2 : gr.h->g.vol; };
     int rows_cap = 0, tiles = 0, nsys_max = 0;
     long nmax = 0;
     for (auto& gr : groups) {
         rows_cap += gr.nsys;
-        tiles += (gr.h->g.vol + TS - 1) / TS;
+        tiles += (nsites(gr) + TS - 1) / TS;
         nsys_max = std::max(nsys_max, gr.nsys);
-        nmax = std::max(nmax, 12L * gr.h->g.vol);
+        nmax = std::max(nmax, 12L * nsites(gr));
     }
     if (rows_cap > 512) throw Error{SEEDCG_ERR_ARG, "at most 512 systems per batch"};
     const int rblocks = (int)std::min<long>((nmax + kRedThreads * 4 - 1) / (kRedThreads * 4), 152 * 8);
@@ -490,10 +579,11 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     size_t need = 1 << 16;
     auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
     for (auto& gr : groups) {
-        const long n = 12L * gr.h->g.vol;
-        for (int k = 0; k < 5; k++) add((size_t)gr.nsys * n * cxR);
-        for (int k = 0; k < 3; k++) add((size_t)gr.nsys * n * sizeof(double2));
-        add((size_t)gr.nsys * ((gr.h->g.vol + TS - 1) / TS) * sizeof(double));
+        const long n = 12L * nsites(gr);
+        for (int k = 0; k < (eo ? 6 : 5); k++) add((size_t)gr.nsys * n * cxR);
+        for (int k = 0; k < 2; k++) add((size_t)gr.nsys * n * sizeof(double2));
+        add((size_t)std::max(gr.nsys, 2) * n * sizeof(double2));
+        add((size_t)gr.nsys * ((nsites(gr) + TS - 1) / TS) * sizeof(double));
     }
     add(sizeof(GroupDev<R>) * kMaxGroups);
     add(sizeof(double) * 8 * rows_cap + sizeof(int) * 8 * rows_cap);
@@ -507,21 +597,23 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     int tile0 = 0;
     for (int f = 0; f < ng; f++) {
         seedcg_handle* h = groups[f].h;
-        const long n = 12L * h->g.vol;
+        const long n = 12L * nsites(groups[f]);
         const int ns = groups[f].nsys;
         gd[f].g = h->g;
         gd[f].u = fp64 ? reinterpret_cast<const cx_t<R>*>(h->u64.p) : reinterpret_cast<const cx_t<R>*>(h->u32.p);
         gd[f].kappa = (R)h->kappa;
         gd[f].n = n;
+        gd[f].eo = eo ? 1 : 0;
         gd[f].xr = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].r = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].p = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].q = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].t = cv.take<cx_t<R>>((size_t)ns * n);
+        gd[f].e = eo ? cv.take<cx_t<R>>((size_t)ns * n) : nullptr;
         Gx[f] = cv.take<double2>((size_t)ns * n);
         MX[f] = cv.take<double2>((size_t)ns * n);
-        T64[f] = cv.take<double2>((size_t)ns * n);
-        gd[f].ntiles = (h->g.vol + TS - 1) / TS;
+        T64[f] = cv.take<double2>((size_t)std::max(ns, 2) * n);
+        gd[f].ntiles = (nsites(groups[f]) + TS - 1) / TS;
         gd[f].part = cv.take<double>((size_t)ns * gd[f].ntiles);
         gd[f].tile0 = tile0;
         tile0 += gd[f].ntiles;
@@ -629,8 +721,13 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
             dim3 gr(rblocks, nf);
             k_mf_ru_flush<R><<<gr, kRedThreads, 0, st>>>(ru_slot, ru_sys, gd[f].xr, groups[f].x64, Gx[f], n);
             SEEDCG_CHECK_LAUNCH();
-            dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, nf, Gx[f], T64[f], st);
-            dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, nf, T64[f], MX[f], st);
+            if (eo) {
+                eo_apply_mdag_m_f64(h->g, h->u64.as<double2>(), h->kappa, nf, Gx[f], T64[f], T64[f] + n,
+                                    MX[f], st);
+            } else {
+                dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 0, nf, Gx[f], T64[f], st);
+                dslash_mrhs_f64(h->g, h->u64.as<double2>(), h->kappa, 1, nf, T64[f], MX[f], st);
+            }
             k_mf_ru_resid<R><<<gr, kRedThreads, 0, st>>>(ru_row, ru_slot, ru_sys, groups[f].b64, MX[f],
                                                          gd[f].r, n, C, trd, C.partials, C.counters);
             SEEDCG_CHECK_LAUNCH();
@@ -714,8 +811,7 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     out.rpb = rpb;
     auto chunk = [&](cudaStream_t s) {
         for (int it = 0; it < poll; it++) {
-            launch_mf<R>(rpb, 0, tiles, s, gdev, ng, rows);
-            launch_mf<R>(rpb, 1, tiles, s, gdev, ng, rows);
+            launch_op<R>(eo, rpb, tiles, s, gdev, ng, rows);
             k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
             dim3 gr(gx, rows_cap);
@@ -746,7 +842,7 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
             SEEDCG_CUDA_TRY(cudaEventRecord(ev, st));
             SEEDCG_CUDA_TRY(cudaStreamWaitEvent(cs, ev, 0));
             SEEDCG_CUDA_TRY(cudaGraphLaunch(gexec, cs));
-            g_kernel_launches.fetch_add((unsigned long long)5 * poll, std::memory_order_relaxed);
+            g_kernel_launches.fetch_add((unsigned long long)(eo ? 7 : 5) * poll, std::memory_order_relaxed);
             SEEDCG_CUDA_TRY(cudaEventRecord(ev, cs));
             SEEDCG_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
             out.graph_chunks++;

@@ -34,6 +34,8 @@ struct seedcg_handle {
     void* pinned = nullptr;       // small pinned host buffer for flag polls
     void* guess = nullptr;        // learned initial guess: weights, Adam state, buffers
     bool force_x0 = false;        // this solve starts from X (set when the guess supplied x_0)
+    bool eo_active = false;       // the running solve is on the even-odd system (half vectors)
+    bool vbasis_eo = false;       // the stored basis holds half vectors of the even-odd system
 };
 
 namespace seedcg {
@@ -58,4 +60,6 @@ seedcg_status project_basis_impl(seedcg_handle* h, int rows, int nvec, const dou
                                  double* C, int use_tc, cudaStream_t st);
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
                          int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st);
+seedcg_status solve_eo_impl(seedcg_handle* h, int nrhs, const double* E, double* X, double tol,
+                            int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st);
 }

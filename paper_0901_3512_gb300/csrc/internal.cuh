@@ -163,6 +163,19 @@ void dslash_mrhs_f64(const Geom& g, const double2* u, double kappa, int dag, int
 void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                      const float2* in, float2* out, cudaStream_t s);
 
+// even-odd preconditioned system (evenodd.cu), FP64 half vectors in the internal layout:
+// out_r = A^dag A x_r, A = 1 - kappa^2 H_oe H_eo (te, y: one even / odd half scratch each)
+void eo_apply_mdag_m_f64(const Geom& g, const double2* u, double kappa, int n, const double2* x,
+                         double2* te, double2* y, double2* out, cudaStream_t st);
+// phi = eta_o + kappa H_oe eta_e and b = A^dag phi for n full fields eta
+void eo_rhs_f64(const Geom& g, const double2* u, double kappa, int n, const double2* eta, double2* phi,
+                double2* b, double2* ee, double2* eo, double2* te, cudaStream_t st);
+// half[r] = the parity-p sites of full[r] for n fields
+void eo_gather_f64(const Geom& g, int p, int n, const double2* full, double2* half, cudaStream_t st);
+// full x from x_o: x_e = eta_e + kappa H_eo x_o
+void eo_reconstruct_f64(const Geom& g, const double2* u, double kappa, int n, const double2* x_odd,
+                        const double2* eta, double2* x, double2* ee, double2* xe, cudaStream_t st);
+
 // the multi-RHS kernel with its default tile shape, never timing alternatives
 void dslash_mrhs_fixed_f64(const Geom& g, const double2* u, double kappa, int dag, int n,
                            const double2* in, double2* out, cudaStream_t s);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "cg_batch.cuh"
+#include "eo.cuh"
 #include "handle.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -70,6 +71,25 @@ __device__ void lz_after_beta(const LzDev& L, int i) {
     if (b <= 1e-14 * fabs(a)) {
         c->breakdown = 1;
         c->m = i;
+    }
+}
+
+// alpha_i is final: the LU recurrence of T (Algorithm 1 steps 3 and 6, Eq. 2)
+__device__ __forceinline__ void lz_alpha_fin(const LzDev& L, int i, double a) {
+    L.alpha[i - 1] = a;
+    if (i == 1) {
+        L.delta[0] = a;
+        L.zeta[0] = L.ctl->beta0;
+    } else {
+        const double bp = L.beta[i - 2];
+        const double gm = bp / L.delta[i - 2];
+        L.gamma[i - 2] = gm;
+        L.delta[i - 1] = a - gm * bp;
+        L.zeta[i - 1] = -gm * L.zeta[i - 2];
+    }
+    if (L.delta[i - 1] == 0.0) {
+        L.ctl->status = SEEDCG_ERR_BREAKDOWN;
+        L.ctl->m = i;
     }
 }
 
@@ -138,24 +158,53 @@ k_lz_Ddag(Geom g, const cx_t<R>* __restrict__ u, R kappa, const cx_t<R>* __restr
         }
         red[0] = (double)part;
     }
-    grid_sum<1>(red, L.partials, L.counters + CTR_B, [&](double* tot) {
-        const double a = tot[0];
-        L.alpha[i - 1] = a;
-        if (i == 1) {
-            L.delta[0] = a;
-            L.zeta[0] = L.ctl->beta0;
+    grid_sum<1>(red, L.partials, L.counters + CTR_B, [&](double* tot) { lz_alpha_fin(L, i, tot[0]); });
+}
+
+// Even-odd system (Section 3): M = A^dag A on odd-site half vectors, A = 1 - kappa^2 H_oe H_eo,
+// applied in four parity-restricted hops per Lanczos iteration:
+//   STAGE 0  e = H_eo v                 (even sites)
+//   STAGE 1  y = v - kappa^2 H_oe e     (A v)
+//   STAGE 2  e = H^dag_eo y
+//   STAGE 3  f = y - kappa^2 H^dag_oe e - beta_{i-1} v_{i-1};  alpha_i = Re v_i^dag f
+//            (the hops of D^dag give A^dag = g5 A g5), with the LU finaliser of k_lz_Ddag.
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_eo(Geom g, const cx_t<R>* __restrict__ u, R kk, const cx_t<R>* __restrict__ other,
+        const cx_t<R>* __restrict__ same, cx_t<R>* __restrict__ out, const cx_t<R>* __restrict__ v,
+        const cx_t<R>* __restrict__ vprev, int i, LzDev L) {
+    constexpr int DAG = STAGE >= 2 ? 1 : 0;
+    constexpr int POUT = (STAGE & 1) ? 1 : 0;
+    if (i > L.ctl->m) return;
+    const int vh = g.vol / 2;
+    const int hh = blockIdx.x * blockDim.x + threadIdx.x;
+    double red[1] = {0.0};
+    if (hh < vh) {
+        Spinor<R> acc;
+        eo_site_apply<R, DAG>(g, u, POUT, hh, other, POUT ? same : nullptr, R(1), POUT ? -kk : R(1), acc);
+        if (STAGE < 3) {
+            store_spinor(out, vh, hh, acc);
         } else {
-            const double bp = L.beta[i - 2];
-            const double gm = bp / L.delta[i - 2];
-            L.gamma[i - 2] = gm;
-            L.delta[i - 1] = a - gm * bp;
-            L.zeta[i - 1] = -gm * L.zeta[i - 2];
+            const R bprev = i > 1 ? (R)L.beta[i - 2] : R(0);
+            R part = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                cx_t<R> fv = acc.c[k / 3][k % 3];
+                const size_t ix = sidx(k, hh, vh);
+                const cx_t<R> vv = v[ix];
+                if (i > 1) {
+                    const cx_t<R> pv = vprev[ix];
+                    fv.x -= bprev * pv.x;
+                    fv.y -= bprev * pv.y;
+                }
+                out[ix] = fv;
+                part += vv.x * fv.x + vv.y * fv.y;
+            }
+            red[0] = (double)part;
         }
-        if (L.delta[i - 1] == 0.0) {
-            L.ctl->status = SEEDCG_ERR_BREAKDOWN;
-            L.ctl->m = i;
-        }
-    });
+    }
+    if (STAGE == 3)
+        grid_sum<1>(red, L.partials, L.counters + CTR_B, [&](double* tot) { lz_alpha_fin(L, i, tot[0]); });
 }
 
 // Steps 4 and 7 (literal seeding): eta^j = v_i^dag r_0^j - gamma_{i-1} eta^j for
@@ -196,29 +245,20 @@ k_lz_eta(const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ r0, long n, 
 }
 
 // Steps 5-7 vector part: f -= alpha_i v_i; beta_i = ||f|| (final unless PO
-// follows).  MODE selects the solution updates of steps 3 and 6-7 done in the
-// same pass:
-//   LZ_LITERAL  w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i, x^1 += zeta_i w_i,
-//               x^j += eta^j w_i, all in R (the literal seeding of FP64 runs);
-//   LZ_X1       w_i in R and x^1 += zeta_i w_i accumulated in FP64 (x1 = the
-//               FP64 solution of RHS 1; the systems j >= 2 take Eq. (1) later).
-enum { LZ_PLAIN = 0, LZ_LITERAL = 1, LZ_X1 = 2 };
-template <typename R, int MODE>
+// follows).  LIT (the literal seeding of FP64 runs) also does, in R, steps 3 and
+// 6-7: w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i, x^1 += zeta_i w_i, x^j += eta^j w_i.
+template <typename R, bool LIT>
 __global__ void __launch_bounds__(kRedThreads)
 k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __restrict__ w,
-            cx_t<R>* __restrict__ X, double2* __restrict__ x1, int nrhs, long n, int i,
-            int final_beta, LzDev L) {
-    constexpr bool LIT = MODE == LZ_LITERAL;
+            cx_t<R>* __restrict__ X, int nrhs, long n, int i, int final_beta, LzDev L) {
     if (i > L.ctl->m) return;
     const R a = (R)L.alpha[i - 1];
-    R dl = 0, bp = 0, zt = 0, idl = 0;
-    if (MODE != LZ_PLAIN) {
+    R dl = 0, bp = 0, zt = 0;
+    if (LIT) {
         dl = (R)L.delta[i - 1];
         bp = i > 1 ? (R)L.beta[i - 2] : R(0);
         zt = (R)L.zeta[i - 1];
-        idl = (R)(1.0 / L.delta[i - 1]);
     }
-    const double zt64 = MODE == LZ_X1 ? L.zeta[i - 1] : 0.0;
     R part = 0;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
          e += (long)gridDim.x * blockDim.x) {
@@ -227,16 +267,6 @@ k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __r
         fv.y -= a * vv.y;
         f[e] = fv;
         part += fv.x * fv.x + fv.y * fv.y;
-        if (MODE == LZ_X1) {
-            cx_t<R> ww = i > 1 ? w[e] : mk<R>(0, 0);
-            ww.x = (vv.x - bp * ww.x) * idl;
-            ww.y = (vv.y - bp * ww.y) * idl;
-            w[e] = ww;
-            double2 xv = x1[e];
-            xv.x = fma(zt64, (double)ww.x, xv.x);
-            xv.y = fma(zt64, (double)ww.y, xv.y);
-            x1[e] = xv;
-        }
         if (LIT) {
             cx_t<R> ww = i > 1 ? w[e] : mk<R>(0, 0);
             ww.x = (vv.x - bp * ww.x) / dl;
@@ -251,6 +281,79 @@ k_lz_update(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __r
                 cx_t<R> xj = X[(size_t)j * n + e];
                 xj = cfma(mk<R>((R)et.x, (R)et.y), ww, xj);
                 X[(size_t)j * n + e] = xj;
+            }
+        }
+    }
+    double red[1] = {(double)part};
+    grid_sum<1>(red, L.partials, L.counters + CTR_D, [&](double* tot) {
+        L.beta[i - 1] = sqrt(tot[0]);
+        if (final_beta) lz_after_beta(L, i);
+    });
+}
+
+// The blocked modes' pass with 16-byte accesses: a thread owns 16 / sizeof(cx_t<R>)
+// consecutive complex entries (two in FP32, one in FP64; n is a multiple of 4).
+// X1: also steps 3 and 6 for RHS 1, w_i = (v_i - beta_{i-1} w_{i-1}) / delta_i in R
+// and x^1 += zeta_i w_i accumulated in FP64 (x1 = the FP64 solution of RHS 1; the
+// systems j >= 2 take Eq. (1) after the run).  X1 = false: f -= alpha v and beta only.
+template <typename R, bool X1>
+__global__ void __launch_bounds__(kRedThreads)
+k_lz_update_v(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* __restrict__ w,
+              double2* __restrict__ x1, long n, int i, int final_beta, LzDev L) {
+    if (i > L.ctl->m) return;
+    constexpr int W = 16 / (int)sizeof(cx_t<R>);
+    const R a = (R)L.alpha[i - 1];
+    R bp = 0, idl = 0;
+    double zt = 0.0;
+    if (X1) {
+        bp = i > 1 ? (R)L.beta[i - 2] : R(0);
+        idl = (R)(1.0 / L.delta[i - 1]);
+        zt = L.zeta[i - 1];
+    }
+    R part = 0;
+    const long ng = n / W;
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < ng; g += (long)gridDim.x * blockDim.x) {
+        cx_t<R> vv[W], fv[W], ww[W];
+        if constexpr (W == 2) {
+            const float4 a4 = reinterpret_cast<const float4*>(v)[g];
+            const float4 b4 = reinterpret_cast<const float4*>(f)[g];
+            vv[0] = mk<R>(a4.x, a4.y); vv[1] = mk<R>(a4.z, a4.w);
+            fv[0] = mk<R>(b4.x, b4.y); fv[1] = mk<R>(b4.z, b4.w);
+            if (X1) {
+                const float4 c4 = i > 1 ? __ldcs(reinterpret_cast<const float4*>(w) + g) : make_float4(0, 0, 0, 0);
+                ww[0] = mk<R>(c4.x, c4.y); ww[1] = mk<R>(c4.z, c4.w);
+            }
+        } else {
+            vv[0] = v[g];
+            fv[0] = f[g];
+            if (X1) ww[0] = i > 1 ? __ldcs(reinterpret_cast<const double2*>(w) + g) : mk<R>(0, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            fv[k].x -= a * vv[k].x;
+            fv[k].y -= a * vv[k].y;
+            part += fv[k].x * fv[k].x + fv[k].y * fv[k].y;
+            if (X1) {
+                ww[k].x = (vv[k].x - bp * ww[k].x) * idl;
+                ww[k].y = (vv[k].y - bp * ww[k].y) * idl;
+            }
+        }
+        // w and x^1 are streamed (evict-first): each is touched once per iteration, and
+        // caching them would push the operator's links and vectors out of L2
+        if constexpr (W == 2) {
+            reinterpret_cast<float4*>(f)[g] = make_float4(fv[0].x, fv[0].y, fv[1].x, fv[1].y);
+            if (X1) __stcs(reinterpret_cast<float4*>(w) + g, make_float4(ww[0].x, ww[0].y, ww[1].x, ww[1].y));
+        } else {
+            f[g] = fv[0];
+            if (X1) __stcs(reinterpret_cast<double2*>(w) + g, make_double2(ww[0].x, ww[0].y));
+        }
+        if (X1) {
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                double2 xv = __ldcs(x1 + g * W + k);
+                xv.x = fma(zt, (double)ww[k].x, xv.x);
+                xv.y = fma(zt, (double)ww[k].y, xv.y);
+                __stcs(x1 + g * W + k, xv);
             }
         }
     }
@@ -577,7 +680,9 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
                         cudaStream_t st, bool run_cg = true) {
     const seedcg_options& o = h->opt;
     const int vol = h->g.vol;
-    const long n = 12L * vol;
+    // the even-odd system (Section 3) works on odd-site half vectors
+    const bool eo = h->eo_active;
+    const long n = 12L * (eo ? vol / 2 : vol);
     const bool fp64 = sizeof(R) == 8;
     const bool literal = (o.seed_mode == 0) && fp64;
     const int m_max = std::max(o.m_max, 1);
@@ -590,9 +695,10 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     const size_t cxR = sizeof(cx_t<R>);
     size_t need = 0;
     auto add = [&](size_t bytes) { need += ((bytes + 255) & ~(size_t)255); };
-    for (int k = 0; k < 5; k++) add(n * cxR);                   // vA f vB t w
+    for (int k = 0; k < 6; k++) add(n * cxR);                   // vA f vB t w e
     for (int k = 0; k < 6; k++) add((size_t)nrhs * n * cxR);    // R0 XR Rr P Q T
-    for (int k = 0; k < 3; k++) add((size_t)nrhs * n * sizeof(double2));  // G MX T64
+    for (int k = 0; k < 2; k++) add((size_t)nrhs * n * sizeof(double2));  // G MX
+    add((size_t)std::max(nrhs, 2) * n * sizeof(double2));                 // T64
     h->work.ensure(need + 8192);
     Carve cv{h->work.as<char>(), 0, h->work.bytes};
     cx_t<R>* vA = cv.take<cx_t<R>>(n);
@@ -600,6 +706,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     cx_t<R>* vB = cv.take<cx_t<R>>(n);
     cx_t<R>* tv = cv.take<cx_t<R>>(n);
     cx_t<R>* wv = cv.take<cx_t<R>>(n);
+    cx_t<R>* ev = cv.take<cx_t<R>>(n);   // even-site intermediate of the even-odd operator
     cx_t<R>* R0 = cv.take<cx_t<R>>((size_t)nrhs * n);
     cx_t<R>* XR = cv.take<cx_t<R>>((size_t)nrhs * n);
     cx_t<R>* Rr = cv.take<cx_t<R>>((size_t)nrhs * n);
@@ -608,7 +715,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     cx_t<R>* Tv = cv.take<cx_t<R>>((size_t)nrhs * n);
     double2* G = cv.take<double2>((size_t)nrhs * n);
     double2* MX = cv.take<double2>((size_t)nrhs * n);
-    double2* T64 = cv.take<double2>((size_t)nrhs * n);
+    double2* T64 = cv.take<double2>((size_t)std::max(nrhs, 2) * n);
     if (fv != vA + n || vB != fv + n)
         throw Error{SEEDCG_ERR_ARG, "internal: working vectors are not contiguous"};
 
@@ -636,9 +743,23 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     SEEDCG_CUDA_TRY(cudaMemsetAsync(L.counters, 0, 8192 * sizeof(unsigned), st));
     // V basis and coefficient scratch
     const size_t vrow = (size_t)n * sizeof(VT);
+    if (h->vbasis.bytes < vrow * (size_t)m_max) {
+        // refuse a basis that cannot fit before allocating it (m_max rows of one vector each)
+        size_t free_b = 0, total_b = 0;
+        SEEDCG_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        if (vrow * (size_t)m_max > free_b + h->vbasis.bytes) {
+            char msg[256];
+            snprintf(msg, sizeof(msg),
+                     "the stored basis needs m_max x %zu B = %.1f GB of device memory, %.1f GB is free; "
+                     "lower m_max or choose a narrower basis precision",
+                     vrow, 1e-9 * (double)(vrow * (size_t)m_max), 1e-9 * (double)(free_b + h->vbasis.bytes));
+            throw Error{SEEDCG_ERR_OOM, msg};
+        }
+    }
     h->vbasis.ensure(vrow * (size_t)m_max);
     VT* Vb = h->vbasis.as<VT>();
     h->vbasis_prec = o.precision;
+    h->vbasis_eo = eo;
     h->vbasis_m = 0;
     const size_t cols = (size_t)std::max(nrhs, 2);
     const size_t coef_elems = ms * cols;
@@ -728,7 +849,10 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     // ---------------- step 1: r_0^j = b^j - M x_0^j ----------------
     const int nbl = std::min<long>((n * nrhs + 255) / 256, 152 * 32);
     if (o.x0_given || h->force_x0) {
-        apply_M64(h, nrhs, X64, T64, MX, st);
+        if (eo)
+            eo_apply_mdag_m_f64(h->g, h->u64.as<double2>(), h->kappa, nrhs, X64, T64, T64 + n, MX, st);
+        else
+            apply_M64(h, nrhs, X64, T64, MX, st);
         k_resid_init<R><<<nbl, 256, 0, st>>>(B64, MX, R0, n * nrhs);
     } else {
         k_resid_init<R><<<nbl, 256, 0, st>>>(B64, nullptr, R0, n * nrhs);
@@ -771,11 +895,25 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
         cx_t<R>* v = vA;
         cx_t<R>* vprev = vB;
         int i = 1;
+        const int sbh = site_blocks(vol / 2);
+        const R kk = (R)(h->kappa * h->kappa);
         for (; i <= m_max; i++) {
-            k_lz_D<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, v, tv, i, L);
-            SEEDCG_CHECK_LAUNCH();
-            k_lz_Ddag<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, tv, v, vprev, fv, i, L);
-            SEEDCG_CHECK_LAUNCH();
+            if (eo) {
+                // f = A^dag A v - beta v_prev, alpha: four half-lattice hops
+                k_lz_eo<R, 0><<<sbh, kRedThreads, 0, st>>>(h->g, U, kk, v, nullptr, ev, nullptr, nullptr, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                k_lz_eo<R, 1><<<sbh, kRedThreads, 0, st>>>(h->g, U, kk, ev, v, tv, nullptr, nullptr, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                k_lz_eo<R, 2><<<sbh, kRedThreads, 0, st>>>(h->g, U, kk, tv, nullptr, ev, nullptr, nullptr, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                k_lz_eo<R, 3><<<sbh, kRedThreads, 0, st>>>(h->g, U, kk, ev, tv, fv, v, vprev, i, L);
+                SEEDCG_CHECK_LAUNCH();
+            } else {
+                k_lz_D<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, v, tv, i, L);
+                SEEDCG_CHECK_LAUNCH();
+                k_lz_Ddag<R><<<sb, kRedThreads, 0, st>>>(h->g, U, kap, tv, v, vprev, fv, i, L);
+                SEEDCG_CHECK_LAUNCH();
+            }
             if (literal) {
                 for (int j0 = 2; j0 <= nrhs; j0 += 8) {
                     int ne = std::min(8, nrhs - j0 + 1);
@@ -786,11 +924,11 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
             }
             const bool po_now = k_po > 0 && i >= 2 && (i % k_po) == 0;
             if (literal)
-                k_lz_update<R, LZ_LITERAL><<<rb, kRedThreads, 0, st>>>(
-                    v, fv, wv, reinterpret_cast<cx_t<R>*>(X64), nullptr, nrhs, n, i, po_now ? 0 : 1, L);
+                k_lz_update<R, true><<<rb, kRedThreads, 0, st>>>(
+                    v, fv, wv, reinterpret_cast<cx_t<R>*>(X64), nrhs, n, i, po_now ? 0 : 1, L);
             else
-                k_lz_update<R, LZ_X1><<<rb, kRedThreads, 0, st>>>(v, fv, wv, nullptr, X64, nrhs, n, i,
-                                                                 po_now ? 0 : 1, L);
+                k_lz_update_v<R, true><<<vec_blocks(n, 16 / (int)sizeof(cx_t<R>)), kRedThreads, 0, st>>>(
+                    v, fv, wv, X64, n, i, po_now ? 0 : 1, L);
             SEEDCG_CHECK_LAUNCH();
             if (po_now) {
                 cudaEvent_t e0, e1;
@@ -1208,7 +1346,7 @@ namespace {
 template <typename R, typename VT>
 seedcg_status classic_rounds(seedcg_handle* h, int nrhs, double2* B64, double2* X64, double tol,
                              int k_po, seedcg_info* info, cudaStream_t st) {
-    const long n = 12L * h->g.vol;
+    const long n = 12L * (h->eo_active ? h->g.vol / 2 : h->g.vol);
     const seedcg_options saved = h->opt;
     const bool x0 = saved.x0_given || h->force_x0;
     std::vector<int> lz(nrhs, 0);
@@ -1419,6 +1557,11 @@ seedcg_status d_residual_rounds(seedcg_handle* h, int nrhs, const double2* E64, 
 
 }  // namespace
 
+namespace {
+seedcg_status dispatch_solve(seedcg_handle* h, int nrhs, double2* B64, double2* X64, double tol,
+                             int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st);
+}
+
 seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X, double tol,
                          int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {
     // B, X: device canonical complex128 (the API layer stages host pointers)
@@ -1467,6 +1610,19 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
             if (!(hn[nrhs + j] < hn[j])) SEEDCG_CUDA_TRY(cudaMemsetAsync(X64 + (size_t)j * n, 0, n * sizeof(double2), st));
         h->force_x0 = true;
     }
+    seedcg_status code = dispatch_solve(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
+    if (dmode)
+        code = d_residual_rounds(h, nrhs, E64, B64, X64, T64, tol, !h->opt.stop_after_seed, code, info, st);
+    from_internal_f64(X64, X, vol, nrhs, st);
+    SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return code;
+}
+
+namespace {
+// the method selected by the options on internal FP64 B64 / X64 (full or, with
+// h->eo_active, odd-site half vectors)
+seedcg_status dispatch_solve(seedcg_handle* h, int nrhs, double2* B64, double2* X64, double tol,
+                             int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {
     seedcg_status code;
     if (h->opt.seed_mode == 3) {
         code = h->opt.precision == SEEDCG_FP64 ? cg_only<double>(h, nrhs, B64, X64, tol, info, st)
@@ -1494,9 +1650,57 @@ seedcg_status solve_impl(seedcg_handle* h, int nrhs, const double* B, double* X,
             code = run_solve<float, __nv_bfloat162>(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
             break;
     }
-    if (dmode)
-        code = d_residual_rounds(h, nrhs, E64, B64, X64, T64, tol, !h->opt.stop_after_seed, code, info, st);
-    from_internal_f64(X64, X, vol, nrhs, st);
+    return code;
+}
+}  // namespace
+
+// Improved Seed-CG on the even-odd preconditioned system of Section 3,
+// A^dag A x_o = A^dag phi with phi = eta_o + kappa H_oe eta_e, on the same
+// device-resident engine as the full-lattice solve (every precision mode and
+// seeding form), then x_e = eta_e + kappa H_eo x_o.  E, X: device canonical
+// complex128 full fields.
+seedcg_status solve_eo_impl(seedcg_handle* h, int nrhs, const double* E, double* X, double tol,
+                            int extra_iters, int reorth_period, seedcg_info* info, cudaStream_t st) {
+    const Geom& g = h->g;
+    const long nh = 12L * (g.vol / 2), nf = 12L * g.vol;
+    // staging: eta and the full solution (full), then phi, b, x_o (half), 3 half scratch
+    const size_t full_b = (size_t)nrhs * nf * sizeof(double2), half_b = (size_t)nrhs * nh * sizeof(double2);
+    h->staging.ensure(2 * full_b + 3 * half_b + 3 * (size_t)nh * sizeof(double2) + 1024);
+    double2* E64 = h->staging.as<double2>();
+    double2* F64 = E64 + (size_t)nrhs * nf;
+    double2* Phi = F64 + (size_t)nrhs * nf;
+    double2* B64 = Phi + (size_t)nrhs * nh;
+    double2* X64 = B64 + (size_t)nrhs * nh;
+    double2* s0 = X64 + (size_t)nrhs * nh;
+    double2* s1 = s0 + nh;
+    double2* s2 = s1 + nh;
+    const double2* u = h->u64.as<double2>();
+    to_internal_f64(E, E64, g.vol, nrhs, st);
+    eo_rhs_f64(g, u, h->kappa, nrhs, E64, Phi, B64, s0, s1, s2, st);
+    if (h->opt.x0_given) {
+        to_internal_f64(X, F64, g.vol, nrhs, st);
+        eo_gather_f64(g, 1, nrhs, F64, X64, st);
+    } else {
+        SEEDCG_CUDA_TRY(cudaMemsetAsync(X64, 0, half_b, st));
+    }
+    struct EoScope {
+        seedcg_handle* h;
+        ~EoScope() { h->eo_active = false; }
+    } scope{h};
+    h->eo_active = true;
+    h->force_x0 = false;
+    seedcg_status code = dispatch_solve(h, nrhs, B64, X64, tol, extra_iters, reorth_period, info, st);
+    h->eo_active = false;
+    eo_reconstruct_f64(g, u, h->kappa, nrhs, X64, E64, F64, s0, s1, st);
+    if (info && info->true_resid_D) {
+        // the residual of the original system D x = eta, as Section 3 monitors it
+        DevBuf tb;
+        tb.ensure(full_b);
+        std::vector<double> ratio;
+        d_residuals(h, nrhs, E64, F64, tb.as<double2>(), ratio, st);
+        for (int j = 0; j < nrhs; j++) info->true_resid_D[j] = ratio[j];
+    }
+    from_internal_f64(F64, X, g.vol, nrhs, st);
     SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
     return code;
 }

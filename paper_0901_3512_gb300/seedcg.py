@@ -315,12 +315,16 @@ def seedcg_solve_eo(h, eta, X, tol: float, extra_iters: int, reorth_period: int,
     iters = (ctypes.c_int * nrhs)()
     mv = (ctypes.c_int * nrhs)()
     tr = (ctypes.c_double * nrhs)()
-    info.iters, info.matvecs, info.true_resid = iters, mv, tr
+    trd = (ctypes.c_double * nrhs)(*([float("nan")] * nrhs))
+    info.iters, info.matvecs, info.true_resid, info.true_resid_D = iters, mv, tr, trd
     code = load().seedcg_solve_eo(h, nrhs, ctypes.c_void_p(_ptr(eta)), ctypes.c_void_p(_ptr(X)), float(tol),
                                   int(extra_iters), int(reorth_period), ctypes.byref(info), _stream_ptr(stream))
     _check(h, code, allow=(SEEDCG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
-    return code, {"m_conv": info.m_conv, "m": info.m, "po_count": info.po_count, "iters": list(iters),
-                  "matvecs": list(mv), "true_resid": list(tr), "ms_total": info.ms_total}
+    return code, {"status": code, "m_conv": info.m_conv, "m": info.m, "po_count": info.po_count,
+                  "cg_iters_max": info.cg_iters_max, "reliable_updates": info.reliable_updates,
+                  "iters": list(iters), "matvecs": list(mv), "true_resid": list(tr),
+                  "true_resid_D": list(trd), "ms_total": info.ms_total, "ms_lanczos": info.ms_lanczos,
+                  "ms_po": info.ms_po, "ms_seed": info.ms_seed, "ms_cg": info.ms_cg}
 
 
 def seedcg_eo_source(h, eta, phi, stream=None):

@@ -78,11 +78,12 @@ def test_eo_rejects_host_pointers():
     s.close()
 
 
-def test_eo_seed_cg_matches_oracle():
-    """Improved Seed-CG on the even-odd system (Section 3's setup) against the
-    oracle's improved_seed_cg on A^dag A (blocked seeds): m_conv, m and the
-    per-system iterations within 2 %, the reconstructed full solutions within
-    1e-6, and D x = eta solved."""
+@pytest.mark.parametrize("seed_mode", [0, 1])
+def test_eo_seed_cg_matches_oracle(seed_mode):
+    """Improved Seed-CG on the even-odd system (Section 3's setup), on the
+    device-resident engine, against the oracle's improved_seed_cg on A^dag A
+    (literal or blocked seeds): m_conv, m and the per-system iterations within
+    2 %, the reconstructed full solutions within 1e-6, and D x = eta solved."""
     need_gpu()
     dims, kappa, tol = (4, 4, 4, 4), 0.21, 1e-10
     u = W.gauge_field(dims, 0.5, 12)
@@ -91,8 +92,9 @@ def test_eo_seed_cg_matches_oracle():
     from oracle.seedcg import improved_seed_cg
     eta = W.point_sources(dims, 2)
     B = np.stack([eo.Adag(eo.source(e)).reshape(-1) for e in eta])
-    ref = improved_seed_cg(eo.M, B, None, tol, 4000, 10, past_factor=1.5, seed_mode="blocked")
-    s = seedcg.Solver(dims, u, kappa, precision="fp64", past_factor=1.5, m_max=4000)
+    ref = improved_seed_cg(eo.M, B, None, tol, 4000, 10, past_factor=1.5,
+                           seed_mode="literal" if seed_mode == 0 else "blocked")
+    s = seedcg.Solver(dims, u, kappa, precision="fp64", past_factor=1.5, m_max=4000, seed_mode=seed_mode)
     X = dev(np.zeros_like(eta))
     code, info = seedcg.seedcg_solve_eo(s.h, dev(eta), X, tol, 0, 10)
     assert code == seedcg.SEEDCG_OK
@@ -101,6 +103,7 @@ def test_eo_seed_cg_matches_oracle():
         return abs(a - b) <= max(1, int(np.ceil(0.02 * max(a, b))))
 
     assert within(info["m_conv"], ref.seed.m_conv) and within(info["m"], ref.seed.m), (info, ref.seed.m)
+    assert info["po_count"] == ref.seed.po_count
     got = host(X)
     for j in range(2):
         assert within(info["iters"][j], int(ref.iters[j])), (info["iters"], ref.iters)
@@ -109,4 +112,90 @@ def test_eo_seed_cg_matches_oracle():
         assert rel(got[j].reshape(-1), want) <= 1e-6
         rd = np.linalg.norm(eta[j].reshape(-1) - op.D(got[j].reshape(-1))) / np.linalg.norm(eta[j])
         assert rd <= 1e-6, rd
+        assert abs(info["true_resid_D"][j] - rd) <= 1e-3 * rd + 1e-15
+        # matvecs in applications of the full-lattice D: 2 per A^dag A
+        assert info["matvecs"][j] >= 2 * info["iters"][j]
+    # the stored basis is the oracle's: odd-site half vectors, orthonormal after PO
+    m = info["m"]
+    vh = W.volume(dims) // 2
+    Vg = dev(np.zeros((m, vh, 4, 3), dtype=np.complex128))
+    seedcg.seedcg_get_basis(s.h, 0, m, Vg)
+    Vg = host(Vg).reshape(m, -1)
+    assert rel(Vg[:20], ref.seed.V[:20]) <= 1e-10
+    last = (m // 10) * 10
+    G = Vg[:last].conj() @ Vg[:last].T
+    assert np.abs(G - np.eye(last)).max() <= 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tc", [("mixed_v32", 1), ("mixed_vbf16", 1), ("mixed_vbf16", 0)])
+def test_eo_mixed_precision_meets_tol(precision, tc):
+    """The even-odd solve in the mixed modes on 4^4: every residual of
+    A^dag A x_o = b, recomputed with the oracle, meets tol, the solutions are
+    within the distance two residuals <= tol allow of the oracle's (2 cond tol,
+    cond of A^dag A from its dense spectrum), and the original system's
+    residual is reported."""
+    need_gpu()
+    from oracle.seedcg import improved_seed_cg
+    from tests.gpu_helpers import recompute_slack
+    dims, kappa, tol = (4, 4, 4, 4), 0.21, 1e-8
+    u = W.gauge_field(dims, 0.5, 12)
+    op = WilsonOperator(dims, u, kappa)
+    eo = EvenOddOperator(op)
+    eta = W.point_sources(dims, 3)
+    B = np.stack([eo.Adag(eo.source(e)).reshape(-1) for e in eta])
+    n = B.shape[1]
+    Md = np.stack([eo.M(e) for e in np.eye(n, dtype=np.complex128)], axis=1)
+    ev = np.linalg.eigvalsh(Md)
+    cond = ev[-1] / ev[0]
+    ref = improved_seed_cg(eo.M, B, None, tol, 4000, 10, past_factor=1.5, seed_mode="blocked")
+    s = seedcg.Solver(dims, u, kappa, precision=precision, past_factor=1.5, m_max=4000, use_tensor_cores=tc)
+    X = dev(np.zeros_like(eta))
+    code, info = seedcg.seedcg_solve_eo(s.h, dev(eta), X, tol, 0, 10)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X)
+    for j in range(3):
+        xo = got[j][eo.odd].reshape(-1)
+        r = np.linalg.norm(B[j] - eo.M(xo)) / np.linalg.norm(B[j])
+        assert r <= tol + recompute_slack(ev[-1], np.linalg.norm(xo), np.linalg.norm(B[j])), (j, r)
+        assert rel(xo, ref.X[j]) <= 2 * cond * tol * 1.001
+        assert np.isfinite(info["true_resid_D"][j])
+    s.close()
+
+
+def test_eo_8x8x8x16_mixed_bf16_point_sources():
+    """The even-odd solve of the 8^3x16 workload (twelve point sources, bf16
+    basis with the tcgen05 seed projection): every residual of the even-odd
+    system recomputed with the oracle's operator meets tol; the original
+    system's residual, recomputed with the oracle's D, equals the reported
+    one; fewer Lanczos iterations than the full-lattice system needs."""
+    need_gpu()
+    from tests.gpu_helpers import recompute_slack
+    wl = W.WORKLOADS["small_8x8x8x16_nrhs12"]
+    f = wl.fields[0]
+    u = f.gauge()
+    kappa = W.kappa_for(f.name)
+    op = WilsonOperator(f.dims, u, kappa)
+    eo = EvenOddOperator(op)
+    eta = wl.sources_for(0)
+    s = seedcg.Solver(f.dims, u, kappa, precision="mixed_vbf16", past_factor=wl.past_factor, m_max=6000)
+    X = dev(np.zeros_like(eta))
+    code, info = seedcg.seedcg_solve_eo(s.h, dev(eta), X, wl.tol, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    got = host(X)
+    lam_max = (1 + 8 * kappa) ** 4      # ||A|| <= 1 + kappa^2 ||H||^2 <= (1 + 8 kappa)^2
+    for j in range(len(eta)):
+        b = eo.Adag(eo.source(eta[j])).reshape(-1)
+        xo = got[j][eo.odd].reshape(-1)
+        r = np.linalg.norm(b - eo.M(xo)) / np.linalg.norm(b)
+        assert r <= wl.tol + recompute_slack(lam_max, np.linalg.norm(xo), np.linalg.norm(b)), (j, r)
+        rd = np.linalg.norm(eta[j].reshape(-1) - op.D(got[j].reshape(-1))) / np.linalg.norm(eta[j])
+        assert abs(info["true_resid_D"][j] - rd) <= 1e-3 * rd + 1e-15
+    # the full-lattice system needs more iterations: textbook CG on D^dag D for RHS 1 (oracle)
+    from oracle.seedcg import cg
+    b1 = op.Ddag(eta[0]).reshape(-1)
+    full_iters = cg(op.M, b1, None, wl.tol, 20000).iters
+    assert info["m_conv"] < full_iters, (info["m_conv"], full_iters)
+    print(f"even-odd 8^3x16 bf16: m_conv {info['m_conv']} m {info['m']} iters {info['iters']} "
+          f"D residuals max {max(info['true_resid_D']):.2e}")
     s.close()

@@ -287,6 +287,58 @@ def test_po_guard_when_orthogonality_is_lost_between_po_steps():
     assert not r10.seed.breakdown and r10.seed.m == r10.seed.m_conv
 
 
+def test_po_guard_reading_from_projection_geometry():
+    """The two tests of the step-8 guard follow from the geometry of one
+    classical Gram-Schmidt pass v' = v - V c, c = V^dag v:
+        ||v'||^2 = ||v||^2 - ||c||^2 + c^dag (G - I) c,   G = V^dag V.
+    (a) For an orthonormal V (G = I) this is Pythagoras: the pass never
+        lengthens a vector, and ||v'|| = ||v|| sin(theta), theta the angle
+        between v and span V.  A pass that lengthens f therefore proves
+        c^dag (G - I) c > ||c||^2: G has an eigenvalue above 2, i.e. some
+        direction is stored twice (a ghost copy) and V is no basis of the
+        Krylov space T describes.  The 1 % margin lies far above the rounding
+        of an orthonormal V in any stored precision (relative 2^-9 in bf16).
+    (b) ||v'|| < 1/2 for a unit v_i means theta < 30 degrees: the Lanczos
+        vector has mostly re-entered the stored space (in exact arithmetic
+        theta = 90 degrees), so the orthogonality lost since the previous PO
+        step is of order one, not of rounding size."""
+    from oracle.seedcg import periodic_reorth
+    rng = np.random.default_rng(21)
+    n, i = 400, 12
+    q, _ = np.linalg.qr(rng.standard_normal((n, i - 1)) + 1j * rng.standard_normal((n, i - 1)))
+    V = np.zeros((i + 1, n), dtype=np.complex128)
+    V[:i - 1] = q.T
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    zp = z - (V[:i - 1].conj() @ z) @ V[:i - 1]
+    zp /= np.linalg.norm(zp)
+    y = V[3] * np.exp(0.4j)                      # a unit vector inside span V
+    for theta_deg in (10.0, 25.0, 29.0, 31.0, 45.0, 80.0):
+        th = np.deg2rad(theta_deg)
+        v = np.sin(th) * zp + np.cos(th) * y          # unit vector at angle theta to span V
+        f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        Vw = V.copy()
+        v2, f2, ok = periodic_reorth(Vw, i, v, f, 1, guard=True)
+        c = V[:i - 1].conj() @ v
+        # Pythagoras for the orthonormal basis, and ||v'|| = sin(theta)
+        vp = v - c @ V[:i - 1]
+        assert abs(np.linalg.norm(vp) ** 2 - (1.0 - np.linalg.norm(c) ** 2)) < 1e-13
+        assert abs(np.linalg.norm(vp) - np.sin(th)) < 1e-13
+        assert ok == (theta_deg > 30.0), theta_deg
+        if ok:   # an orthonormal basis never lengthens f
+            assert np.linalg.norm(f2) <= np.linalg.norm(f) * (1 + 1e-14)
+    # a direction stored twice (G's top eigenvalue 2) is the borderline: along it the
+    # pass keeps the length; stored three times (eigenvalue 3) the pass lengthens f
+    f = 2.0 * V[0] + 0.05 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    for copies, grows in ((2, False), (3, True)):
+        Vd = V.copy()
+        for k in range(1, copies):
+            Vd[i - 1 - k] = V[0]
+        fd = f - (Vd[:i - 1].conj() @ f) @ Vd[:i - 1]
+        G = Vd[:i - 1].conj() @ Vd[:i - 1].T
+        assert abs(np.linalg.eigvalsh(G).max() - copies) < 1e-12
+        assert (np.linalg.norm(fd) > 1.01 * np.linalg.norm(f)) == grows, copies
+
+
 def test_classic_repeated_seeding():
     """The comparison variant (Section 1): every round's seed system runs D-Lanczos
     from its seeded guess, which is textbook CG from that guess (same iteration
