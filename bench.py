@@ -73,6 +73,9 @@ def _args():
     p.add_argument("--kappa", type=float, default=None, help="with --sweep: kappa of the field")
     p.add_argument("--po-passes", type=int, default=1, choices=[1, 2],
                    help="with --sweep: Gram-Schmidt passes per PO step (2 = CGS2)")
+    p.add_argument("--po-guard", type=int, default=1, choices=[0, 1],
+                   help="with --sweep: 0 runs step 8 as printed, without the guard that ends "
+                        "Lanczos when a PO step finds the basis far from orthonormal")
     p.add_argument("--kappas", default="", help="with --sweep kappa: comma-separated values")
     p.add_argument("--guess-eval", action="store_true",
                    help="learned initial guess on the workload's field: train on (b, x) pairs the "
@@ -736,7 +739,7 @@ def run_sweep(args):
 
     def run(kappa, pf, k, nrhs=2):
         s = seedcg.Solver(f.dims, gauge, kappa, precision=prec, past_factor=pf, m_max=args.m_max,
-                          po_passes=args.po_passes)
+                          po_passes=args.po_passes, po_guard=args.po_guard)
         eta = torch.from_numpy(eta_all[2 - nrhs:]).cuda()
         B = torch.empty_like(eta)
         s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
@@ -763,7 +766,7 @@ def run_sweep(args):
     kappa = args.kappa if args.kappa is not None else W.kappa_for(f.name)
     cg0 = plain_cg(kappa)
     base = {"workload": args.workload, "lattice": list(f.dims), "kappa": kappa, "precision": prec,
-            "po_passes": args.po_passes,
+            "po_passes": args.po_passes, "po_guard": args.po_guard,
             "tol": wl.tol, "plain_cg_iters_rhs2": cg0, "plain_cg_matvecs_rhs2": 2 * cg0}
     settings = ([(pf, 10) for pf in (1.0, 1.2, 1.4, 1.6, 2.0)] if args.sweep == "m"
                 else [(1.4, k) for k in (10, 100, 200, 250, 0)])

@@ -100,6 +100,13 @@ typedef struct {
                               recomputed in FP64, is the binding criterion: systems that miss
                               it continue CG with a tighter M tolerance (up to six rounds).
                               seedcg_solve only. */
+    int po_guard;          /* 1 (default): a PO step (Algorithm 1 step 8) that finds the stored
+                              basis far from orthonormal ends the Lanczos run at i - 1: a
+                              projection pass leaving ||v_i|| < 1/2 (v_i within 30 degrees of
+                              the stored space), or re-orthogonalisation lengthening f by more
+                              than 1 % (impossible for an orthonormal basis).  0: step 8 runs
+                              as printed whatever it finds (the run still ends if v_i vanishes
+                              or a scalar is not finite). */
 } seedcg_options;
 
 typedef struct {

@@ -67,11 +67,12 @@ class LanczosSeedResult:
 def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optional[np.ndarray],
                  tol: float, m_max: int, reorth_period: int, past_factor: float = 1.0,
                  extra_iters: int = 0, po_passes: int = 1,
-                 keep_x1_history: bool = False) -> LanczosSeedResult:
+                 keep_x1_history: bool = False, po_guard: bool = True) -> LanczosSeedResult:
     """Algorithm 1, steps 1-9, for the first right-hand side, seeding the others.
 
     B: [nrhs][N] right-hand sides; X0: initial guesses (None = zero).
-    reorth_period = k (0 = never).  Returns the seeded X and all scalars.
+    reorth_period = k (0 = never).  po_guard = False runs step 8 as printed,
+    ending the run only if v_i vanishes.  Returns the seeded X and all scalars.
     """
     B = np.asarray(B, dtype=np.complex128)
     nrhs, n = B.shape
@@ -169,8 +170,14 @@ def seed_lanczos(M: Callable[[np.ndarray], np.ndarray], B: np.ndarray, X0: Optio
         # of the stored space, an order-one loss of orthogonality.
         if reorth_period > 0 and i % reorth_period == 0:
             beta_pre = _norm(f)
-            v_po, f_po, ok = periodic_reorth(V, i, v, f, po_passes, guard=True)
-            if not ok or not (_norm(f_po) <= 1.01 * beta_pre):
+            if po_guard:
+                v_po, f_po, ok = periodic_reorth(V, i, v, f, po_passes, guard=True)
+                broken = not ok or not (_norm(f_po) <= 1.01 * beta_pre)
+            else:
+                with np.errstate(all="ignore"):
+                    v_po, f_po = periodic_reorth(V, i, v, f, po_passes)
+                broken = not (np.all(np.isfinite(v_po)) and np.isfinite(_norm(f_po)))
+            if broken:
                 breakdown = True
                 i -= 1
                 break
@@ -330,12 +337,13 @@ class SolveResult:
 
 
 def improved_seed_cg(M, B, X0, tol, m_max, reorth_period, past_factor=1.0, extra_iters=0,
-                     po_passes=1, seed_mode="literal", cg_maxiter=100000) -> SolveResult:
+                     po_passes=1, seed_mode="literal", cg_maxiter=100000, po_guard=True) -> SolveResult:
     """Seed once with RHS 1 past convergence (Section 2, improvements 1-3),
     then standard CG for every system whose true residual exceeds tol."""
     B = np.asarray(B, dtype=np.complex128)
     nrhs = B.shape[0]
-    res = seed_lanczos(M, B, X0, tol, m_max, reorth_period, past_factor, extra_iters, po_passes)
+    res = seed_lanczos(M, B, X0, tol, m_max, reorth_period, past_factor, extra_iters, po_passes,
+                       po_guard=po_guard)
     if seed_mode == "blocked":
         # Eq. (1) is the closed form of steps 4 and 7 for the systems j >= 2; the
         # first system's x^1 is the one steps 3 and 6 build by the LU recurrence

@@ -49,6 +49,7 @@ bool valid_options(const seedcg_options& o, std::string& why) {
     if (o.use_tensor_cores < 0 || o.use_tensor_cores > 2) { why = "use_tensor_cores must be 0, 1 or 2"; return false; }
     if (o.use_guess < 0 || o.use_guess > 1) { why = "use_guess must be 0 or 1"; return false; }
     if (o.resid_mode < 0 || o.resid_mode > 1) { why = "resid_mode must be 0 or 1"; return false; }
+    if (o.po_guard < 0 || o.po_guard > 1) { why = "po_guard must be 0 or 1"; return false; }
     return true;
 }
 
@@ -72,6 +73,7 @@ void seedcg_default_options(seedcg_options* opt) {
     opt->use_tensor_cores = 1;
     opt->use_guess = 0;
     opt->resid_mode = 0;
+    opt->po_guard = 1;
 }
 
 seedcg_status seedcg_create(seedcg_handle** out, const int dims[4], const double* gauge,

@@ -39,6 +39,13 @@ constexpr int TS = 32;       // sites per dslash tile (one warp per right-hand s
 // right-hand sides processed side by side per tile (warps per block): picked
 // per batch by the autotuner below from {4, 8, 12}
 
+// brick tiling of one field's lattice: Lx x by x bz sites at one t per tile
+// (x neighbours always in the tile, most y and z neighbours too); n = 0 when
+// the lattice admits no brick of that many sites
+struct Brk {
+    int bx, by, bz, ny, nz, n;
+};
+
 template <typename R>
 struct GroupDev {
     Geom g;
@@ -56,6 +63,7 @@ struct GroupDev {
     int ntiles;
     int tile0;          // first tile of this group in the dslash grid
     int row0;           // first global row of this group
+    Brk b64, b128;      // brick tilings of 64 and 128 sites (single-field full-lattice batches)
 };
 
 struct Rows {
@@ -220,6 +228,100 @@ k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
         if (DOT) {
             const double d = (double)warp_sum_t(dr);
             if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
+        }
+    }
+}
+
+// 1/2 for a batch of one full-lattice field: the same D / D^dag [+ dot] over brick
+// tiles of TB sites (TB / 32 warps per right-hand-side group, RPB groups per block).
+// The brick's links (U_mu(x) and U_mu(x - mu), scaled by -kappa and the boundary
+// sign) are staged once in shared memory and reused by every right-hand side;
+// the neighbours in x (always) and mostly in y and z are sites of the same
+// brick, so their spinor loads hit in L1.
+template <typename R, int DAG, bool DOT, int TB, int RPB>
+__global__ void __launch_bounds__(TB * RPB, (sizeof(R) == 4 && TB * RPB <= 256) ? 3 : 1)
+k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double sdot[TB * RPB / 32];
+    cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);   // [2][4][9][TB]
+    int* ss = reinterpret_cast<int*>(sl + 72 * TB);         // [TB] site
+    int* sbk = ss + TB;                                     // [4][TB] x - mu
+    R* sg = reinterpret_cast<R*>(sbk + 4 * TB);             // [2][TB]
+    const GroupDev<R>& gd = G[0];
+    const int nsys = rows.nact[0];
+    if (nsys == 0) return;
+    const Brk br = TB == 64 ? gd.b64 : gd.b128;
+    const Geom g = gd.g;
+    const int vol = g.vol;
+    const R kappa = gd.kappa;
+    int b = blockIdx.x;
+    const int iy = b % br.ny;
+    b /= br.ny;
+    const int iz = b % br.nz;
+    const int t = b / br.nz;
+    if (threadIdx.x < TB) {
+        const int j = threadIdx.x;
+        const int x = j % br.bx, dy = (j / br.bx) % br.by, dz = j / (br.bx * br.by);
+        const int s = x + g.stride[1] * (iy * br.by + dy) + g.stride[2] * (iz * br.bz + dz) + g.stride[3] * t;
+        ss[j] = s;
+        const Nbr nb = neighbours(g, s);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) sbk[mu * TB + j] = nb.b[mu];
+        sg[j] = nb.fwrap_t ? kappa : -kappa;
+        sg[TB + j] = nb.bwrap_t ? kappa : -kappa;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 72 * TB; e += blockDim.x) {
+        const int j = e % TB;
+        const int c = (e / TB) % 9;
+        const int mu = (e / (9 * TB)) % 4;
+        const int dir = e / (36 * TB);
+        const cx_t<R> z = __ldg(gd.u + (size_t)(mu * 9 + c) * vol + (dir ? sbk[mu * TB + j] : ss[j]));
+        sl[e] = cscale(z, mu == 3 ? sg[dir * TB + j] : -kappa);
+    }
+    __syncthreads();
+    const int j = threadIdx.x % TB;
+    const int q = threadIdx.x / TB;
+    const int s = ss[j];
+    const Nbr nb = neighbours(g, s);
+    auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TB + j]; };
+    auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TB + j]; };
+    const cx_t<R>* in = DAG ? gd.t : gd.p;
+    cx_t<R>* out = DAG ? gd.q : gd.t;
+    const int passes = (nsys + RPB - 1) / RPB;
+    for (int pass = 0; pass < passes; pass++) {
+        const int r = pass * RPB + q;
+        R dr = 0;
+        if (r < nsys) {
+            const cx_t<R>* inr = in + (size_t)r * gd.n;
+            Spinor<R> res;
+            auto load = [&](int y, Spinor<R>& sp) { load_spinor(inr, vol, y, sp); };
+            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+            store_spinor(out + (size_t)r * gd.n, vol, s, res);
+            if (DOT) {
+                const cx_t<R>* pr = gd.p + (size_t)r * gd.n;
+                R acc = 0;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
+                    const cx_t<R> rz = res.c[k / 3][k % 3];
+                    acc += pz.x * rz.x + pz.y * rz.y;
+                }
+                dr = acc;
+            }
+        }
+        if (DOT) {
+            // TB / 32 warps share r: warp sums in the working precision, then a
+            // fixed-order FP64 sum of the brick's warps
+            const double d = (double)warp_sum_t(dr);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) sdot[threadIdx.x >> 5] = d;
+            __syncthreads();
+            if (threadIdx.x < RPB && pass * RPB + (int)threadIdx.x < nsys) {
+                double tsum = 0.0;
+                for (int w = 0; w < TB / 32; w++) tsum += sdot[threadIdx.x * (TB / 32) + w];
+                gd.part[(size_t)(pass * RPB + threadIdx.x) * gd.ntiles + blockIdx.x] = tsum;
+            }
         }
     }
 }
@@ -439,15 +541,75 @@ void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<
     SEEDCG_CHECK_LAUNCH();
 }
 
+template <typename R, int DAG, bool DOT, int TB, int RPB>
+void brick_launch(int nb, cudaStream_t s, const GroupDev<R>* gdev, Rows rows) {
+    const size_t smem = (size_t)TB * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
+    static bool attr = false;
+    if (!attr) {
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_mf_brick<R, DAG, DOT, TB, RPB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_mf_brick<R, DAG, DOT, TB, RPB><<<nb, TB * RPB, smem, s>>>(gdev, rows);
+    SEEDCG_CHECK_LAUNCH();
+}
+
+// Launch shape of the operator, chosen by the autotuner: codes 4, 8, 12 are the
+// multi-field kernel with that many warps per tile of TS sites; code TB * 1000 +
+// RPB is the brick kernel of TB sites with RPB right-hand-side groups (one field).
+constexpr bool is_brick_code(int code) { return code >= 1000; }
+
 // q = M p for every active system: 2 launches (D, D^dag) or 4 (even-odd hops)
 template <typename R>
-void launch_op(bool eo, int rpb, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+void launch_op(bool eo, int code, int tiles, const Brk& b64, const Brk& b128, cudaStream_t s,
+               const GroupDev<R>* gdev, int ng, Rows rows) {
     if (eo) {
-        for (int stage = 0; stage < 4; stage++) launch_mf_eo<R>(rpb, stage, tiles, s, gdev, ng, rows);
+        for (int stage = 0; stage < 4; stage++) launch_mf_eo<R>(code, stage, tiles, s, gdev, ng, rows);
+    } else if (is_brick_code(code)) {
+        switch (code) {
+            case 64004:
+                brick_launch<R, 0, false, 64, 4>(b64.n, s, gdev, rows);
+                brick_launch<R, 1, true, 64, 4>(b64.n, s, gdev, rows);
+                break;
+            case 64008:
+                brick_launch<R, 0, false, 64, 8>(b64.n, s, gdev, rows);
+                brick_launch<R, 1, true, 64, 8>(b64.n, s, gdev, rows);
+                break;
+            case 128002:
+                brick_launch<R, 0, false, 128, 2>(b128.n, s, gdev, rows);
+                brick_launch<R, 1, true, 128, 2>(b128.n, s, gdev, rows);
+                break;
+            default:
+                brick_launch<R, 0, false, 128, 4>(b128.n, s, gdev, rows);
+                brick_launch<R, 1, true, 128, 4>(b128.n, s, gdev, rows);
+                break;
+        }
     } else {
-        launch_mf<R>(rpb, 0, tiles, s, gdev, ng, rows);
-        launch_mf<R>(rpb, 1, tiles, s, gdev, ng, rows);
+        launch_mf<R>(code, 0, tiles, s, gdev, ng, rows);
+        launch_mf<R>(code, 1, tiles, s, gdev, ng, rows);
     }
+}
+
+int largest_divisor_le(int L, int cap) {
+    int best = 1;
+    for (int d = 1; d <= L && d <= cap; d++)
+        if (L % d == 0) best = d;
+    return best;
+}
+
+// the brick of about `cap` sites for g: Lx x by x bz, by preferring a share of
+// the y extent before z (n = 0 when it does not come to exactly TB sites)
+Brk brick_for(const Geom& g, int tb) {
+    Brk b{};
+    b.bx = g.L[0];
+    if (b.bx > 64 || b.bx > tb) return b;
+    b.by = largest_divisor_le(g.L[1], (tb / 2 > b.bx ? tb / 2 : tb) / b.bx);
+    b.bz = largest_divisor_le(g.L[2], tb / (b.bx * b.by));
+    if (b.bx * b.by * b.bz != tb) return Brk{};
+    b.ny = g.L[1] / b.by;
+    b.nz = g.L[2] / b.bz;
+    b.n = b.ny * b.nz * g.L[3];
+    return b;
 }
 
 std::string tune_key(const std::vector<CgGroup>& groups, bool fp64) {
@@ -496,25 +658,29 @@ std::vector<std::pair<std::string, int>>& tune_table() {
 }
 
 template <typename R>
-int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const GroupDev<R>* gdev, int ng,
-                 Rows rows, cudaStream_t st) {
+int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const Brk& b64, const Brk& b128,
+                 const GroupDev<R>* gdev, int ng, Rows rows, cudaStream_t st) {
     const std::string key = tune_key(groups, sizeof(R) == 8);
     {
         std::lock_guard<std::mutex> lk(tune_mutex());
         for (auto& e : tune_table())
             if (e.first == key) return e.second;
     }
-    const int cands[3] = {4, 8, 12};
+    const bool eo = groups[0].h->eo_active;
+    std::vector<int> cands{4, 8, 12};
+    if (!eo && ng == 1) {
+        if (b64.n) cands.insert(cands.end(), {64004, 64008});
+        if (b128.n) cands.insert(cands.end(), {128002, 128004});
+    }
     cudaEvent_t a, b;
     SEEDCG_CUDA_TRY(cudaEventCreate(&a));
     SEEDCG_CUDA_TRY(cudaEventCreate(&b));
     int best = 8;
     float best_ms = 1e30f;
-    const bool eo = groups[0].h->eo_active;
     for (int c : cands) {
-        launch_op<R>(eo, c, tiles, st, gdev, ng, rows);  // warm-up
+        launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows);  // warm-up
         SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
-        for (int r = 0; r < 3; r++) launch_op<R>(eo, c, tiles, st, gdev, ng, rows);
+        for (int r = 0; r < 3; r++) launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows);
         SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -614,6 +780,10 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
         MX[f] = cv.take<double2>((size_t)ns * n);
         T64[f] = cv.take<double2>((size_t)std::max(ns, 2) * n);
         gd[f].ntiles = (nsites(groups[f]) + TS - 1) / TS;
+        gd[f].b64 = (ng == 1 && !eo) ? brick_for(h->g, 64) : Brk{};
+        gd[f].b128 = (ng == 1 && !eo) ? brick_for(h->g, 128) : Brk{};
+        if (std::max(gd[f].b64.n, gd[f].b128.n) > gd[f].ntiles)
+            throw Error{SEEDCG_ERR_ARG, "internal: more bricks than site tiles"};
         gd[f].part = cv.take<double>((size_t)ns * gd[f].ntiles);
         gd[f].tile0 = tile0;
         tile0 += gd[f].ntiles;
@@ -807,11 +977,17 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
 
     // ---- the iteration chunk (graph-captured) ----
     const int gx = rblocks;
-    const int rpb = nrows > 0 ? autotune_rpb<R>(groups, tiles, gdev, ng, rows, st) : 8;
+    const Brk b64 = gd[0].b64, b128 = gd[0].b128;
+    const int rpb = nrows > 0 ? autotune_rpb<R>(groups, tiles, b64, b128, gdev, ng, rows, st) : 8;
     out.rpb = rpb;
+    if (is_brick_code(rpb)) {
+        // the step-length shares now come from one entry per brick
+        gd[0].ntiles = rpb / 1000 == 64 ? b64.n : b128.n;
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(gdev, gd.data(), sizeof(GroupDev<R>), cudaMemcpyHostToDevice, st));
+    }
     auto chunk = [&](cudaStream_t s) {
         for (int it = 0; it < poll; it++) {
-            launch_op<R>(eo, rpb, tiles, s, gdev, ng, rows);
+            launch_op<R>(eo, rpb, tiles, b64, b128, s, gdev, ng, rows);
             k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
             dim3 gr(gx, rows_cap);

@@ -17,7 +17,7 @@ struct LzCtl {
     int po_count;
     int m_max;
     int extra_iters;
-    int pad;
+    int guard;        // 1: the step-8 guard may end the run (seedcg_options.po_guard)
     double beta0;     // ||r_0^1||
     double bnorm1;    // ||b^1||
     double tol;

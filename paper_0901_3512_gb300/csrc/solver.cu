@@ -416,7 +416,8 @@ __device__ __forceinline__ void po_check_nv(const LzDev& L, int i, double nv2) {
     // v_i is a unit vector; if the projection removed most of it the basis no
     // longer spans what the recurrence assumes (numerical invariant subspace or
     // a basis stored too coarsely): end the run at i - 1, before this vector.
-    if (!(nv >= 0.5)) {
+    // Without the guard only a vanished (or non-finite) v_i ends it.
+    if (L.ctl->guard ? !(nv >= 0.5) : !(nv > 0.0 && isfinite(nv))) {
         L.ctl->breakdown = 2;
         L.ctl->m = i - 1;
     }
@@ -540,7 +541,7 @@ k_po_finish(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int 
         L.ctl->po_count += 1;
         // an orthogonal projection never lengthens f; growth means the stored
         // basis is far from orthonormal: end the run at i - 1
-        if (!(bnew <= 1.01 * L.beta[i - 1])) {
+        if (L.ctl->guard ? !(bnew <= 1.01 * L.beta[i - 1]) : !isfinite(bnew)) {
             L.ctl->breakdown = 3;
             L.ctl->m = i - 1;
             return;
@@ -874,6 +875,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
         hc.extra_iters = extra_iters;
         hc.tol = tol;
         hc.past_factor = o.past_factor;
+        hc.guard = o.po_guard ? 1 : 0;
         // copy everything but beta0 / bnorm1 (set on the device)
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(L.ctl, &hc, offsetof(LzCtl, beta0), cudaMemcpyHostToDevice, st));
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(&L.ctl->tol, &hc.tol, sizeof(double) * 2, cudaMemcpyHostToDevice, st));

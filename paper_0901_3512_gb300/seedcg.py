@@ -40,7 +40,7 @@ class seedcg_options(ctypes.Structure):
                 ("x0_given", ctypes.c_int), ("cg_maxiter", ctypes.c_int),
                 ("stop_after_seed", ctypes.c_int), ("poll_every", ctypes.c_int),
                 ("use_tensor_cores", ctypes.c_int), ("use_guess", ctypes.c_int),
-                ("resid_mode", ctypes.c_int)]
+                ("resid_mode", ctypes.c_int), ("po_guard", ctypes.c_int)]
 
 
 class seedcg_info(ctypes.Structure):

@@ -321,6 +321,35 @@ def test_po_guard_when_orthogonality_is_lost():
     s.close()
 
 
+def test_po_step8_as_printed_without_the_guard():
+    """po_guard = 0 runs step 8 as printed at k = 100 on the near-critical 4^4
+    field: the basis loses orthogonality between PO steps, the oracle's run
+    continues far past where the guard would stop it and never converges.  As
+    with the guard, past the loss of orthogonality the trajectory depends on
+    rounding, so only the first hundred Lanczos scalars are compared with the
+    oracle; the rest must be valid: finite solutions, every true residual <=
+    tol, and a run that did not converge by the recurrence (m_conv = 0) but
+    went past the guard's stopping point."""
+    need_gpu()
+    dims, u, op, eta, B = _near_critical(2)
+    ref = seed_lanczos(op.M, B, None, TOL, 8000, 100, 2.0, po_guard=False)
+    assert ref.m_conv == 0 and ref.m > 1000
+    s = seedcg.Solver(dims, u, 0.23, past_factor=2.0, precision="fp64", po_guard=0, m_max=8000)
+    X = dev(np.zeros_like(eta))
+    code, info = s.solve(_gpu_B(s, eta), X, TOL, 0, 100)
+    assert code == seedcg.SEEDCG_OK
+    assert info["m_conv"] == 0 and info["m"] > 1000
+    a, b, d, m = seedcg.seedcg_get_lanczos(s.h, 10000)
+    assert np.allclose(a[:100], ref.alpha[:100], rtol=1e-8, atol=0)
+    assert np.allclose(b[:100], ref.beta[:100], rtol=1e-8, atol=0)
+    got = host(X).reshape(2, -1)
+    assert np.all(np.isfinite(got))
+    for j in range(2):
+        tr = np.linalg.norm(B[j] - op.M(got[j])) / np.linalg.norm(B[j])
+        assert info["true_resid"][j] <= TOL and tr <= TOL * (1 + 1e-6)
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed_v32"])
 def test_original_system_residual_is_binding(precision):
     """resid_mode = 1: B holds eta of D x = eta; the residual Section 3 monitors,
