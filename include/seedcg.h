@@ -302,8 +302,12 @@ seedcg_status seedcg_deflate_guess(seedcg_handle* h, int nev, int nr, const doub
  * parts after layers 1 and 2; input b/||b||, output times ||b||.
  * Weights: complex128 (host) [11520] = layer 1 [9][8][1][4][4], layer 2
  * [9][8][8][4][4], layer 3 [9][1][8][4][4], directions 0, +x,-x,+y,-y,+z,-z,+t,-t.
- * B, X, X0: host or device, complex128 [n][V][4][3].  Computed in FP32 with
- * FP64 reductions.
+ * B, X, X0: host or device, complex128 [n][V][4][3].  Storage is bf16 (the
+ * activations, their gradients and the weights the layers read), accumulation
+ * FP32; the 8 -> 8 layer's contraction (K = 288 complex terms per output) runs on
+ * the tcgen05 tensor cores, forward and backward through the data; Adam keeps
+ * FP32 master weights (what guess_get_weights returns) and sums the gradient
+ * in FP64.  SEEDCG_ERR_TIMEOUT if a bounded tensor-core wait expired.
  */
 seedcg_status seedcg_guess_set_weights(seedcg_handle* h, const double* w);
 seedcg_status seedcg_guess_get_weights(seedcg_handle* h, double* w);
