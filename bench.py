@@ -93,9 +93,10 @@ def _args():
                    help="the even-odd preconditioned system of Section 3 (A^dag A x_o = A^dag phi on "
                         "odd-site half vectors) on the same workload: its own JSON line with its PO "
                         "roofline, beside one full-lattice solve of the same sources (not a bench line)")
-    p.add_argument("--only", default=None, choices=["dslash", "po"],
-                   help="profiling aid: run only the 12-RHS dslash timing, or one solve capped "
-                        "at --m-max Lanczos iterations (re-orthogonalisation kernels)")
+    p.add_argument("--only", default=None, choices=["dslash", "po", "guess"],
+                   help="profiling aid: run only the 12-RHS dslash timing, one solve capped "
+                        "at --m-max Lanczos iterations (re-orthogonalisation kernels), or --steps "
+                        "forward passes of the learned guess on the workload's field")
     return p.parse_args()
 
 
@@ -396,6 +397,50 @@ def run_batch(args):
     replicas.finish()
 
 
+BATCH_WORKLOAD = "batch3_uneven_nrhs24_12_6"
+
+
+def batch3_once():
+    """The three uneven gauge fields (8^3x16 / 12^3x24 / 16^3x32, Z2 sources 24 / 12 / 6) in one
+    seedcg_batch_solve in the workload's own precision (FP32 iteration, FP64 reliable updates):
+    one warm-up call (autotuning), one timed call."""
+    import torch
+    from paper_0901_3512_gb300 import seedcg, workloads as W
+    wl = W.WORKLOADS[BATCH_WORKLOAD]
+    prec = wl.precision
+    solvers, Bs, Xs = [], [], []
+    for i, f in enumerate(wl.fields):
+        sv = seedcg.Solver(f.dims, f.gauge(), W.kappa_for(f.name), precision=prec,
+                           past_factor=wl.past_factor, m_max=4000)
+        eta = torch.from_numpy(wl.sources_for(i)).cuda()
+        B = torch.empty_like(eta)
+        sv.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        solvers.append(sv)
+        Bs.append(B)
+        Xs.append(torch.zeros_like(B))
+    hs = [sv.h for sv in solvers]
+    seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period, allow_not_converged=True)
+    for x in Xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record()
+    code, infos = seedcg.seedcg_batch_solve(hs, Bs, Xs, wl.tol, 0, wl.reorth_period, allow_not_converged=True)
+    eb.record()
+    torch.cuda.synchronize()
+    out = {"workload": BATCH_WORKLOAD, "precision": prec, "seconds": ea.elapsed_time(eb) / 1000.0,
+           "status": code, "systems": sum(wl.nrhs),
+           "fields": [{"lattice": list(f.dims), "nrhs": n, "m_conv": i["m_conv"], "m": i["m"],
+                       "cg_iters_max": i["cg_iters_max"], "max_true_resid": max(i["true_resid"])}
+                      for f, n, i in zip(wl.fields, wl.nrhs, infos)],
+           "ms_cg_batched": infos[0]["ms_cg"]}
+    for sv in solvers:
+        sv.close()
+    del Bs, Xs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -507,6 +552,8 @@ def run_ours(args):
 
     fp64_cmp = None
     cg_only_cmp = None
+    eo_cmp = None
+    batch_cmp = None
     if not args.no_compare and rank == 0 and args.workload == DEFAULT_WORKLOAD:
         # the same 12 systems by standard batched CG from x0 = 0 (no Lanczos, no seeds):
         # what seeding buys on this field (untimed by the line)
@@ -524,6 +571,21 @@ def run_ours(args):
                        "seeded_over_cg_only_time": (ms_max / 1000.0) / tcg}
         s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max)
         del Xc
+        # the even-odd system of Section 3 on the same sources (one warm-up, one timed solve)
+        Xe = torch.zeros_like(eta)
+        seedcg.seedcg_solve_eo(s.h, eta, Xe, wl.tol, 0, k, stream=stream, allow_not_converged=True)
+        Xe.zero_()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        ce, ie = seedcg.seedcg_solve_eo(s.h, eta, Xe, wl.tol, 0, k, stream=stream, allow_not_converged=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        te = ea.elapsed_time(eb) / 1000.0
+        eo_cmp = {"seconds": te, "status": ce, "m_conv": ie["m_conv"], "m": ie["m"],
+                  "cg_iters_max": ie["cg_iters_max"], "ms_po": ie["ms_po"], "ms_cg": ie["ms_cg"],
+                  "max_true_resid": max(ie["true_resid"]), "max_true_resid_D": max(ie["true_resid_D"]),
+                  "speedup_over_full_lattice": (ms_max / 1000.0) / te}
+        del Xe
         # one plain FP64 Improved Seed-CG solve of the same systems on the GPU, for the
         # mixed-precision speed-up (the stored FP64 basis takes ~100 GB: the mixed solver's
         # basis is released first)
@@ -545,6 +607,7 @@ def run_ours(args):
         s64.close()
         del X64
         torch.cuda.empty_cache()
+        batch_cmp = batch3_once()
 
     classic_cmp = None
     if args.compare_classic and rank == 0:
@@ -613,6 +676,10 @@ def run_ours(args):
             out["fp64_plain"] = fp64_cmp
         if cg_only_cmp:
             out["cg_only"] = cg_only_cmp
+        if eo_cmp:
+            out["even_odd"] = eo_cmp
+        if batch_cmp:
+            out["batch3_uneven"] = batch_cmp
         if classic_cmp is not None:
             out["classic_seeding"] = classic_cmp
         print(json.dumps(out))
@@ -712,6 +779,21 @@ def run_only(args):
     if args.only == "dslash":
         ms = s.time_dslash(prec=1, n=wl.nrhs[0], reps=max(args.steps, 1))
         print(json.dumps({"only": "dslash", "ms": ms}))
+    elif args.only == "guess":
+        seedcg.seedcg_guess_set_weights(s.h, W.guess_weights(7))
+        eta = torch.from_numpy(W.z2_sources(f.dims, 1, f.seed, f.field_index, stream=100)).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        X0 = torch.zeros_like(B)
+        seedcg.seedcg_guess_predict(s.h, B, X0)                # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            seedcg.seedcg_guess_predict(s.h, B, X0)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "guess", "ms_per_forward": e0.elapsed_time(e1) / max(args.steps, 1)}))
     else:
         eta = torch.from_numpy(wl.sources_for(0)).cuda()
         B = torch.empty_like(eta)

@@ -8,8 +8,8 @@
 //   2. the same kernel for q = D^dag t, fused with the per-tile share of
 //      Re p^dag q for the step length
 //   3. alpha_j = ||r_j||^2 / p_j^dag q_j          (one block per system)
-//   4. x += alpha p, r -= alpha q, ||r||^2, beta   (rows = systems)
-//   5. p = r + beta p
+//   4. r -= alpha q, ||r||^2, beta                 (rows = systems)
+//   5. x += alpha p, p = r + beta p                (one pass over p for both)
 // A chunk of `poll` iterations is captured once as a CUDA graph and replayed;
 // the kernels read the active-system tables from device memory, so the graph
 // stays valid while systems converge and are compacted away.  Between chunks
@@ -332,7 +332,12 @@ __global__ void __launch_bounds__(256)
 k_mf_alpha(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     const int row = blockIdx.x;
     const int f = rows.group[row];
-    if (f < 0 || !C.active[row]) return;
+    if (f < 0) return;
+    if (!C.active[row]) {
+        // a system that stopped keeps its x: the x update of k_mf_xp adds 0 p
+        if (threadIdx.x == 0) C.alpha[row] = 0.0;
+        return;
+    }
     const GroupDev<R>& gd = G[f];
     const double* part = gd.part + (size_t)rows.local[row] * gd.ntiles;
     double v[1] = {0.0};
@@ -373,27 +378,24 @@ __device__ __forceinline__ void rowsum(double (&v)[NV], double* partials, unsign
     }
 }
 
-// 4: x += alpha p, r -= alpha q, ||r||^2, beta and the per-row flags
+// 4: r -= alpha q, ||r||^2, beta and the per-row flags; the x update
+// waits for k_mf_xp, which reads p once for both x and the new p
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads)
-k_mf_xr(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+k_mf_r(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     const int row = blockIdx.y;
     const int f = rows.group[row];
     if (f < 0 || !C.active[row]) return;
     const GroupDev<R>& gd = G[f];
     const size_t off = (size_t)rows.local[row] * gd.n;
-    cx_t<R>* x = gd.xr + off;
     cx_t<R>* r = gd.r + off;
-    const cx_t<R>* p = gd.p + off;
     const cx_t<R>* w = gd.q + off;
     const R a = (R)C.alpha[row];
     R part = 0;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
          e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> pv = p[e], wv = w[e], xv = x[e], rv = r[e];
-        xv.x += a * pv.x; xv.y += a * pv.y;
+        cx_t<R> wv = w[e], rv = r[e];
         rv.x -= a * wv.x; rv.y -= a * wv.y;
-        x[e] = xv;
         r[e] = rv;
         part += rv.x * rv.x + rv.y * rv.y;
     }
@@ -418,20 +420,26 @@ k_mf_xr(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     });
 }
 
-// 5: p = r + beta p
+// 5: x += alpha p and p = r + beta p in one pass over p.  Rows that
+// stopped in this iteration's k_mf_r still take their last x update; rows stopped
+// earlier have alpha = 0 (their p changes, but it is not used again).
 template <typename R>
-__global__ void k_mf_p(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+__global__ void k_mf_xp(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     const int row = blockIdx.y;
     const int f = rows.group[row];
-    if (f < 0 || !C.active[row]) return;
+    if (f < 0) return;
     const GroupDev<R>& gd = G[f];
     const size_t off = (size_t)rows.local[row] * gd.n;
+    cx_t<R>* x = gd.xr + off;
     const cx_t<R>* r = gd.r + off;
     cx_t<R>* p = gd.p + off;
-    const R b = (R)C.beta[row];
+    const R a = (R)C.alpha[row], b = (R)C.beta[row];
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
          e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> rv = r[e], pv = p[e];
+        cx_t<R> pv = p[e], xv = x[e];
+        const cx_t<R> rv = r[e];
+        xv.x += a * pv.x; xv.y += a * pv.y;
+        x[e] = xv;
         pv.x = rv.x + b * pv.x;
         pv.y = rv.y + b * pv.y;
         p[e] = pv;
@@ -991,9 +999,9 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
             k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
             dim3 gr(gx, rows_cap);
-            k_mf_xr<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
+            k_mf_r<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
-            k_mf_p<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
+            k_mf_xp<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
         }
     };
