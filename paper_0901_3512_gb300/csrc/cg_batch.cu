@@ -4,11 +4,12 @@
 // Every iteration is five launches whatever the number of fields or systems:
 //   1. one multi-field multi-RHS dslash  t = D p   (tiles of 32 sites of every
 //      field; each tile stages its links once, scaled by -kappa and the
-//      boundary sign, and applies them to all of the field's active systems)
-//   2. the same kernel for q = D^dag t, fused with the per-tile share of
-//      Re p^dag q for the step length
-//   3. alpha_j = ||r_j||^2 / p_j^dag q_j          (one block per system)
-//   4. r -= alpha q, ||r||^2, beta                 (rows = systems)
+//      boundary sign, and applies them to all of the field's active systems),
+//      with one share per warp of ||t||^2 = p^dag M p
+//   2. alpha_j = ||r_j||^2 / ||D p_j||^2         (one block per system)
+//   3. the same kernel for D^dag t, whose result q never leaves the registers:
+//      r -= alpha q at the site, with one share per warp of the new ||r||^2
+//   4. beta_j = ||r_j||^2 (new) / ||r_j||^2 (old) and the per-system flags
 //   5. x += alpha p, p = r + beta p                (one pass over p for both)
 // A chunk of `poll` iterations is captured once as a CUDA graph and replayed;
 // the kernels read the active-system tables from device memory, so the graph
@@ -57,12 +58,11 @@ struct GroupDev {
     cx_t<R>* xr;        // [cap][n] iterate increments since the last reliable update
     cx_t<R>* r;
     cx_t<R>* p;
-    cx_t<R>* q;
     cx_t<R>* t;
-    double* part;       // [cap][ntiles] shares of p^dag q
-    int ntiles;
+    double* part;       // [cap][ntiles] shares of ||D p||^2 = p^dag M p (||A p||^2 even-odd)
+    double* part2;      // [cap][ntiles] shares of ||r||^2 after the update of step 3
+    int ntiles;         // tiles of 32 (half-)sites; every share is one warp's sum
     int tile0;          // first tile of this group in the dslash grid
-    int row0;           // first global row of this group
     Brk b64, b128;      // brick tilings of 64 and 128 sites (single-field full-lattice batches)
 };
 
@@ -70,6 +70,7 @@ struct Rows {
     int* group;   // [rows_cap] group of the row, -1 when unused
     int* local;   // [rows_cap] system slot within its group
     int* nact;    // [kMaxGroups] active systems of each group (slots 0..nact-1)
+    int* first;   // [kMaxGroups] row of slot 0 of each group (rows run in group order)
 };
 
 struct CgS {
@@ -85,6 +86,7 @@ struct CgS {
     unsigned* counters;
     double tol, delta2;
     int maxiter;
+    int rows_cap;   // rows of every per-row array (grid of the per-row kernels)
 };
 
 __device__ __forceinline__ int find_group(int b, int ng, const int* tile0) {
@@ -93,12 +95,44 @@ __device__ __forceinline__ int find_group(int b, int ng, const int* tile0) {
     return f;
 }
 
+// The two epilogues of the operator kernels (one thread = one site of one system):
+// after D, the site's ||t||^2; after D^dag, r -= alpha q at the site and its new
+// ||r||^2.  Each warp's sum (32 sites of one system) is one share, written to
+// shares[slot * ntiles + tile32]; k_mf_alpha / k_mf_beta add a system's shares in
+// a fixed order, so no block barrier is needed and the result is reproducible.
+template <typename R>
+__device__ __forceinline__ R r_update_site(cx_t<R>* rr, int vol, int s, const Spinor<R>& q, R a) {
+    Spinor<R> v;
+    load_spinor_rw(rr, vol, s, v);
+    R acc = 0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        cx_t<R>& z = v.c[k / 3][k % 3];
+        const cx_t<R> w = q.c[k / 3][k % 3];
+        z.x -= a * w.x;
+        z.y -= a * w.y;
+        acc += z.x * z.x + z.y * z.y;
+    }
+    store_spinor(rr, vol, s, v);
+    return acc;
+}
+
+__device__ __forceinline__ void put_share(double* shares, int ntiles, int slot, int tile32, float v) {
+    const double d = (double)warp_sum_t(v);
+    if ((threadIdx.x & 31) == 0) shares[(size_t)slot * ntiles + tile32] = d;
+}
+__device__ __forceinline__ void put_share(double* shares, int ntiles, int slot, int tile32, double v) {
+    const double d = warp_sum_t(v);
+    if ((threadIdx.x & 31) == 0) shares[(size_t)slot * ntiles + tile32] = d;
+}
+
 // ---------------------------------------------------------------------------
-// 1/2: multi-field multi-RHS dslash (DAG = 0: t = D p; DAG = 1: q = D^dag t [+ dot])
+// 1/3: multi-field multi-RHS dslash (DAG = 0: t = D p and ||t||^2;
+//      DAG = 1: q = D^dag t, r -= alpha q and ||r||^2)
 // ---------------------------------------------------------------------------
-template <typename R, int DAG, bool DOT, int RPB>
+template <typename R, int DAG, int RPB>
 __global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? (RPB <= 8 ? 3 : 2) : 1))
-k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
+k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     __shared__ cx_t<R> sl[2][4][9][TS];
     __shared__ int sb[4][TS];
     __shared__ R sgn[2][TS];
@@ -148,7 +182,6 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
     auto fl = [&](int mu, int e) { return sl[0][mu][e][j]; };
     auto bl = [&](int mu, int e) { return sl[1][mu][e][j]; };
     const cx_t<R>* in = DAG ? gd.t : gd.p;
-    cx_t<R>* out = DAG ? gd.q : gd.t;
     for (int r = qg; r < nsys; r += RPB) {
         R dr = 0;
         if (live) {
@@ -156,37 +189,26 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
             Spinor<R> res;
             auto load = [&](int y, Spinor<R>& sp) { load_spinor(inr, vol, y, sp); };
             wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
-            store_spinor(out + (size_t)r * gd.n, vol, s, res);
-            if (DOT) {
-                const cx_t<R>* pr = gd.p + (size_t)r * gd.n;
-                R acc = 0;
-#pragma unroll
-                for (int k = 0; k < 12; k++) {
-                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
-                    const cx_t<R> rz = res.c[k / 3][k % 3];
-                    acc += pz.x * rz.x + pz.y * rz.y;
-                }
-                dr = acc;
+            if (DAG) {
+                dr = r_update_site(gd.r + (size_t)r * gd.n, vol, s, res, (R)C.alpha[rows.first[f] + r]);
+            } else {
+                store_spinor(gd.t + (size_t)r * gd.n, vol, s, res);
+                dr = spinor_norm2(res);
             }
         }
-        if (DOT) {
-            // lanes in the working precision, tiles in FP64 (k_mf_alpha)
-            const double d = (double)warp_sum_t(dr);
-            if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
-        }
+        put_share(DAG ? gd.part2 : gd.part, gd.ntiles, r, tile, dr);
     }
 }
 
-// 1-2 for the even-odd system: M p = A^dag A p in four parity-restricted hops over
+// 1/3 for the even-odd system: M p = A^dag A p in four parity-restricted hops over
 // every active system of every field (tiles of TS odd / even half sites):
-//   STAGE 0  e = H_eo p;  1  t = p - kappa^2 H_oe e;  2  e = H^dag_eo t;
-//   STAGE 3  q = t - kappa^2 H^dag_oe e, with the tile shares of Re p^dag q
+//   STAGE 0  e = H_eo p;  1  t = p - kappa^2 H_oe e = A p, and ||A p||^2 = p^dag M p;
+//   STAGE 2  e = H^dag_eo t;  3  q = t - kappa^2 H^dag_oe e, r -= alpha q and ||r||^2
 template <typename R, int STAGE, int RPB>
 __global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? 2 : 1))
-k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
+k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     constexpr int DAG = STAGE >= 2 ? 1 : 0;
     constexpr int POUT = (STAGE & 1) ? 1 : 0;
-    constexpr bool DOT = STAGE == 3;
     __shared__ int s_tile0[kMaxGroups];
     if (threadIdx.x < ng) s_tile0[threadIdx.x] = G[threadIdx.x].tile0;
     __syncthreads();
@@ -204,7 +226,7 @@ k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
     const R kk = gd.kappa * gd.kappa;
     const cx_t<R>* in = STAGE == 0 ? gd.p : STAGE == 2 ? gd.t : gd.e;
     const cx_t<R>* same = STAGE == 1 ? gd.p : STAGE == 3 ? gd.t : nullptr;
-    cx_t<R>* out = (STAGE == 0 || STAGE == 2) ? gd.e : STAGE == 1 ? gd.t : gd.q;
+    cx_t<R>* out = (STAGE == 0 || STAGE == 2) ? gd.e : gd.t;   // STAGE 3 stores nothing
     for (int r = qg; r < nsys; r += RPB) {
         R dr = 0;
         if (live) {
@@ -212,37 +234,28 @@ k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows) {
             Spinor<R> acc;
             eo_site_apply<R, DAG>(g, gd.u, POUT, hh, in + off, POUT ? same + off : nullptr, R(1),
                                   POUT ? -kk : R(1), acc);
-            store_spinor(out + off, vh, hh, acc);
-            if (DOT) {
-                const cx_t<R>* pr = gd.p + off;
-                R acc2 = 0;
-#pragma unroll
-                for (int k = 0; k < 12; k++) {
-                    const cx_t<R> pz = __ldg(pr + sidx(k, hh, vh));
-                    const cx_t<R> rz = acc.c[k / 3][k % 3];
-                    acc2 += pz.x * rz.x + pz.y * rz.y;
-                }
-                dr = acc2;
+            if (STAGE == 3) {
+                dr = r_update_site(gd.r + off, vh, hh, acc, (R)C.alpha[rows.first[f] + r]);
+            } else {
+                store_spinor(out + off, vh, hh, acc);
+                if (STAGE == 1) dr = spinor_norm2(acc);
             }
         }
-        if (DOT) {
-            const double d = (double)warp_sum_t(dr);
-            if (j == 0) gd.part[(size_t)r * gd.ntiles + tile] = d;
-        }
+        if (STAGE == 1 || STAGE == 3) put_share(STAGE == 1 ? gd.part : gd.part2, gd.ntiles, r, tile, dr);
     }
 }
 
-// 1/2 for a batch of one full-lattice field: the same D / D^dag [+ dot] over brick
+// 1/3 for a batch of one full-lattice field: the same two kernels over brick
 // tiles of TB sites (TB / 32 warps per right-hand-side group, RPB groups per block).
 // The brick's links (U_mu(x) and U_mu(x - mu), scaled by -kappa and the boundary
 // sign) are staged once in shared memory and reused by every right-hand side;
 // the neighbours in x (always) and mostly in y and z are sites of the same
-// brick, so their spinor loads hit in L1.
-template <typename R, int DAG, bool DOT, int TB, int RPB>
+// brick, so their spinor loads hit in L1.  The bricks tile the lattice, so the
+// warps of brick b are the 32-site tiles b * TB / 32 ... of the shares.
+template <typename R, int DAG, int TB, int RPB>
 __global__ void __launch_bounds__(TB * RPB, (sizeof(R) == 4 && TB * RPB <= 256) ? 3 : 1)
-k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows) {
+k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ double sdot[TB * RPB / 32];
     cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);   // [2][4][9][TB]
     int* ss = reinterpret_cast<int*>(sl + 72 * TB);         // [TB] site
     int* sbk = ss + TB;                                     // [4][TB] x - mu
@@ -283,50 +296,37 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows) {
     const int j = threadIdx.x % TB;
     const int q = threadIdx.x / TB;
     const int s = ss[j];
+    const int tile32 = blockIdx.x * (TB / 32) + (j >> 5);
     const Nbr nb = neighbours(g, s);
     auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TB + j]; };
     auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TB + j]; };
     const cx_t<R>* in = DAG ? gd.t : gd.p;
-    cx_t<R>* out = DAG ? gd.q : gd.t;
-    const int passes = (nsys + RPB - 1) / RPB;
-    for (int pass = 0; pass < passes; pass++) {
-        const int r = pass * RPB + q;
-        R dr = 0;
-        if (r < nsys) {
-            const cx_t<R>* inr = in + (size_t)r * gd.n;
-            Spinor<R> res;
-            auto load = [&](int y, Spinor<R>& sp) { load_spinor(inr, vol, y, sp); };
-            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
-            store_spinor(out + (size_t)r * gd.n, vol, s, res);
-            if (DOT) {
-                const cx_t<R>* pr = gd.p + (size_t)r * gd.n;
-                R acc = 0;
-#pragma unroll
-                for (int k = 0; k < 12; k++) {
-                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
-                    const cx_t<R> rz = res.c[k / 3][k % 3];
-                    acc += pz.x * rz.x + pz.y * rz.y;
-                }
-                dr = acc;
-            }
+    // a warp's 32 threads share one system: the loop bound is warp-uniform
+    for (int r = q; r < nsys; r += RPB) {
+        const cx_t<R>* inr = in + (size_t)r * gd.n;
+        Spinor<R> res;
+        auto load = [&](int y, Spinor<R>& sp) { load_spinor(inr, vol, y, sp); };
+        wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+        R dr;
+        if (DAG) {
+            dr = r_update_site(gd.r + (size_t)r * gd.n, vol, s, res, (R)C.alpha[rows.first[0] + r]);
+        } else {
+            store_spinor(gd.t + (size_t)r * gd.n, vol, s, res);
+            dr = spinor_norm2(res);
         }
-        if (DOT) {
-            // TB / 32 warps share r: warp sums in the working precision, then a
-            // fixed-order FP64 sum of the brick's warps
-            const double d = (double)warp_sum_t(dr);
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) sdot[threadIdx.x >> 5] = d;
-            __syncthreads();
-            if (threadIdx.x < RPB && pass * RPB + (int)threadIdx.x < nsys) {
-                double tsum = 0.0;
-                for (int w = 0; w < TB / 32; w++) tsum += sdot[threadIdx.x * (TB / 32) + w];
-                gd.part[(size_t)(pass * RPB + threadIdx.x) * gd.ntiles + blockIdx.x] = tsum;
-            }
-        }
+        put_share(DAG ? gd.part2 : gd.part, gd.ntiles, r, tile32, dr);
     }
 }
 
-// 3: alpha = rr / sum of the tile shares (one block per row, fixed order)
+// a row's shares, summed in a fixed order (one block per row)
+__device__ __forceinline__ double row_shares(const double* __restrict__ sh, int ntiles) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < ntiles; b += blockDim.x) v[0] += sh[b];
+    block_sum<1>(v);
+    return v[0];
+}
+
+// 2: alpha = ||r||^2 / ||D p||^2 (one block per row)
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_mf_alpha(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
@@ -334,16 +334,40 @@ k_mf_alpha(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     const int f = rows.group[row];
     if (f < 0) return;
     if (!C.active[row]) {
-        // a system that stopped keeps its x: the x update of k_mf_xp adds 0 p
+        // a system that stopped keeps its x and r: the updates of steps 3 and 5 add 0
         if (threadIdx.x == 0) C.alpha[row] = 0.0;
         return;
     }
     const GroupDev<R>& gd = G[f];
-    const double* part = gd.part + (size_t)rows.local[row] * gd.ntiles;
-    double v[1] = {0.0};
-    for (int b = threadIdx.x; b < gd.ntiles; b += blockDim.x) v[0] += part[b];
-    block_sum<1>(v);
-    if (threadIdx.x == 0) C.alpha[row] = C.rr[row] / v[0];
+    const double den = row_shares(gd.part + (size_t)rows.local[row] * gd.ntiles, gd.ntiles);
+    if (threadIdx.x == 0) C.alpha[row] = C.rr[row] / den;
+}
+
+// 4: beta = the new ||r||^2 over the old, and the per-row flags (one block per row)
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_mf_beta(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+    const int row = blockIdx.x;
+    const int f = rows.group[row];
+    if (f < 0 || !C.active[row]) return;
+    const GroupDev<R>& gd = G[f];
+    const double rn = row_shares(gd.part2 + (size_t)rows.local[row] * gd.ntiles, gd.ntiles);
+    if (threadIdx.x != 0) return;
+    C.beta[row] = rn / C.rr[row];
+    C.rr[row] = rn;
+    C.iters[row] += 1;
+    if (!isfinite(rn)) {
+        C.flag[row] = 3;
+        C.active[row] = 0;
+    } else if (sqrt(rn) <= C.tol * C.bn[row]) {
+        C.flag[row] = 2;
+        C.active[row] = 0;
+    } else if (C.iters[row] >= C.maxiter) {
+        C.flag[row] = 3;
+        C.active[row] = 0;
+    } else if (C.delta2 > 0.0 && rn < C.delta2 * C.rr_ru[row]) {
+        C.flag[row] = 1;
+    }
 }
 
 // per-row grid reduction (grid = (blocks, rows); row = blockIdx.y)
@@ -378,71 +402,73 @@ __device__ __forceinline__ void rowsum(double (&v)[NV], double* partials, unsign
     }
 }
 
-// 4: r -= alpha q, ||r||^2, beta and the per-row flags; the x update
-// waits for k_mf_xp, which reads p once for both x and the new p
+// W consecutive complex entries in one 16-byte access (two in FP32, one in FP64;
+// every vector length n = 12 * sites is even, and every vector starts 16-byte aligned)
+template <typename R> struct Pack16;
+template <> struct Pack16<float> {
+    using T = float4;
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void split(const float4& a, float2 (&o)[2]) {
+        o[0] = make_float2(a.x, a.y);
+        o[1] = make_float2(a.z, a.w);
+    }
+    __device__ __forceinline__ static float4 join(const float2 (&o)[2]) {
+        return make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    }
+};
+template <> struct Pack16<double> {
+    using T = double2;
+    static constexpr int W = 1;
+    __device__ __forceinline__ static void split(const double2& a, double2 (&o)[1]) { o[0] = a; }
+    __device__ __forceinline__ static double2 join(const double2 (&o)[1]) { return o[0]; }
+};
+
+// 5: x += alpha p and p = r + beta p in one pass over p.  Rows that stopped in
+// this iteration's step 4 still take their last x update; rows stopped earlier
+// have alpha = 0 (their p changes, but it is not used again).  16-byte accesses,
+// two groups per thread and trip with all six loads issued first.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads)
-k_mf_r(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
-    const int row = blockIdx.y;
-    const int f = rows.group[row];
-    if (f < 0 || !C.active[row]) return;
-    const GroupDev<R>& gd = G[f];
-    const size_t off = (size_t)rows.local[row] * gd.n;
-    cx_t<R>* r = gd.r + off;
-    const cx_t<R>* w = gd.q + off;
-    const R a = (R)C.alpha[row];
-    R part = 0;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> wv = w[e], rv = r[e];
-        rv.x -= a * wv.x; rv.y -= a * wv.y;
-        r[e] = rv;
-        part += rv.x * rv.x + rv.y * rv.y;
-    }
-    double red[1] = {(double)part};
-    rowsum<1>(red, C.partials, C.counters, [&](double* tot) {
-        const double rn = tot[0];
-        C.beta[row] = rn / C.rr[row];
-        C.rr[row] = rn;
-        C.iters[row] += 1;
-        if (!isfinite(rn)) {
-            C.flag[row] = 3;
-            C.active[row] = 0;
-        } else if (sqrt(rn) <= C.tol * C.bn[row]) {
-            C.flag[row] = 2;
-            C.active[row] = 0;
-        } else if (C.iters[row] >= C.maxiter) {
-            C.flag[row] = 3;
-            C.active[row] = 0;
-        } else if (C.delta2 > 0.0 && rn < C.delta2 * C.rr_ru[row]) {
-            C.flag[row] = 1;
-        }
-    });
-}
-
-// 5: x += alpha p and p = r + beta p in one pass over p.  Rows that
-// stopped in this iteration's k_mf_r still take their last x update; rows stopped
-// earlier have alpha = 0 (their p changes, but it is not used again).
-template <typename R>
-__global__ void k_mf_xp(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+k_mf_xp(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
+    using P = Pack16<R>;
+    using T = typename P::T;
+    constexpr int W = P::W;
     const int row = blockIdx.y;
     const int f = rows.group[row];
     if (f < 0) return;
     const GroupDev<R>& gd = G[f];
     const size_t off = (size_t)rows.local[row] * gd.n;
-    cx_t<R>* x = gd.xr + off;
-    const cx_t<R>* r = gd.r + off;
-    cx_t<R>* p = gd.p + off;
+    T* __restrict__ x = reinterpret_cast<T*>(gd.xr + off);
+    const T* __restrict__ r = reinterpret_cast<const T*>(gd.r + off);
+    T* __restrict__ p = reinterpret_cast<T*>(gd.p + off);
     const R a = (R)C.alpha[row], b = (R)C.beta[row];
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < gd.n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> pv = p[e], xv = x[e];
-        const cx_t<R> rv = r[e];
-        xv.x += a * pv.x; xv.y += a * pv.y;
-        x[e] = xv;
-        pv.x = rv.x + b * pv.x;
-        pv.y = rv.y + b * pv.y;
-        p[e] = pv;
+    const long ng = gd.n / W;
+    const long st = (long)gridDim.x * blockDim.x;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ng; e += 2 * st) {
+        const long e2 = e + st;
+        const bool two = e2 < ng;
+        cx_t<R> pv[2][W], xv[2][W], rv[2][W];
+        P::split(p[e], pv[0]);
+        P::split(x[e], xv[0]);
+        P::split(r[e], rv[0]);
+        if (two) {
+            P::split(p[e2], pv[1]);
+            P::split(x[e2], xv[1]);
+            P::split(r[e2], rv[1]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (h == 1 && !two) break;
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                xv[h][k].x += a * pv[h][k].x;
+                xv[h][k].y += a * pv[h][k].y;
+                pv[h][k].x = rv[h][k].x + b * pv[h][k].x;
+                pv[h][k].y = rv[h][k].y + b * pv[h][k].y;
+            }
+            x[h ? e2 : e] = P::join(xv[h]);
+            p[h ? e2 : e] = P::join(pv[h]);
+        }
     }
 }
 
@@ -522,10 +548,11 @@ k_norm_rows(const T* __restrict__ base, long n, double* partials, unsigned* coun
 // when SEEDCG_TUNE_CACHE names a file, in that file ("key rpb" lines).
 // ---------------------------------------------------------------------------
 template <typename R>
-void launch_mf(int rpb, int dag, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+void launch_mf(int rpb, int dag, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows,
+               const CgS& C) {
 #define SEEDCG_MF(RP)                                                                          \
-    if (dag) k_mf_dslash<R, 1, true, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows);           \
-    else k_mf_dslash<R, 0, false, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows);
+    if (dag) k_mf_dslash<R, 1, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C);               \
+    else k_mf_dslash<R, 0, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C);
     if (rpb == 4) { SEEDCG_MF(4) }
     else if (rpb == 12) { SEEDCG_MF(12) }
     else { SEEDCG_MF(8) }
@@ -534,13 +561,14 @@ void launch_mf(int rpb, int dag, int tiles, cudaStream_t s, const GroupDev<R>* g
 }
 
 template <typename R>
-void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows) {
+void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<R>* gdev, int ng, Rows rows,
+                  const CgS& C) {
 #define SEEDCG_MFE(RP)                                                                          \
     switch (stage) {                                                                           \
-        case 0: k_mf_eo<R, 0, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
-        case 1: k_mf_eo<R, 1, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
-        case 2: k_mf_eo<R, 2, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;            \
-        default: k_mf_eo<R, 3, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows); break;           \
+        case 0: k_mf_eo<R, 0, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C); break;         \
+        case 1: k_mf_eo<R, 1, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C); break;         \
+        case 2: k_mf_eo<R, 2, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C); break;         \
+        default: k_mf_eo<R, 3, RP><<<tiles, TS * RP, 0, s>>>(gdev, ng, rows, C); break;        \
     }
     if (rpb == 4) { SEEDCG_MFE(4) }
     else if (rpb == 12) { SEEDCG_MFE(12) }
@@ -549,16 +577,16 @@ void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<
     SEEDCG_CHECK_LAUNCH();
 }
 
-template <typename R, int DAG, bool DOT, int TB, int RPB>
-void brick_launch(int nb, cudaStream_t s, const GroupDev<R>* gdev, Rows rows) {
+template <typename R, int DAG, int TB, int RPB>
+void brick_launch(int nb, cudaStream_t s, const GroupDev<R>* gdev, Rows rows, const CgS& C) {
     const size_t smem = (size_t)TB * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
     static bool attr = false;
     if (!attr) {
-        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_mf_brick<R, DAG, DOT, TB, RPB>,
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_mf_brick<R, DAG, TB, RPB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    k_mf_brick<R, DAG, DOT, TB, RPB><<<nb, TB * RPB, smem, s>>>(gdev, rows);
+    k_mf_brick<R, DAG, TB, RPB><<<nb, TB * RPB, smem, s>>>(gdev, rows, C);
     SEEDCG_CHECK_LAUNCH();
 }
 
@@ -567,34 +595,36 @@ void brick_launch(int nb, cudaStream_t s, const GroupDev<R>* gdev, Rows rows) {
 // RPB is the brick kernel of TB sites with RPB right-hand-side groups (one field).
 constexpr bool is_brick_code(int code) { return code >= 1000; }
 
-// q = M p for every active system: 2 launches (D, D^dag) or 4 (even-odd hops)
+// steps 1 and 3 of an iteration for every active system: 2 launches (D, D^dag)
+// or 4 (even-odd hops); step 2 (alpha) runs between them in the iteration proper
 template <typename R>
 void launch_op(bool eo, int code, int tiles, const Brk& b64, const Brk& b128, cudaStream_t s,
-               const GroupDev<R>* gdev, int ng, Rows rows) {
+               const GroupDev<R>* gdev, int ng, Rows rows, const CgS& C, bool with_alpha) {
+    auto alpha = [&]() {
+        if (!with_alpha) return;
+        k_mf_alpha<R><<<C.rows_cap, 256, 0, s>>>(gdev, rows, C);
+        SEEDCG_CHECK_LAUNCH();
+    };
     if (eo) {
-        for (int stage = 0; stage < 4; stage++) launch_mf_eo<R>(code, stage, tiles, s, gdev, ng, rows);
+        for (int stage = 0; stage < 2; stage++) launch_mf_eo<R>(code, stage, tiles, s, gdev, ng, rows, C);
+        alpha();
+        for (int stage = 2; stage < 4; stage++) launch_mf_eo<R>(code, stage, tiles, s, gdev, ng, rows, C);
     } else if (is_brick_code(code)) {
+#define SEEDCG_BRICK(TB, RP, BR)                                                               \
+    brick_launch<R, 0, TB, RP>(BR.n, s, gdev, rows, C);                                        \
+    alpha();                                                                                   \
+    brick_launch<R, 1, TB, RP>(BR.n, s, gdev, rows, C);
         switch (code) {
-            case 64004:
-                brick_launch<R, 0, false, 64, 4>(b64.n, s, gdev, rows);
-                brick_launch<R, 1, true, 64, 4>(b64.n, s, gdev, rows);
-                break;
-            case 64008:
-                brick_launch<R, 0, false, 64, 8>(b64.n, s, gdev, rows);
-                brick_launch<R, 1, true, 64, 8>(b64.n, s, gdev, rows);
-                break;
-            case 128002:
-                brick_launch<R, 0, false, 128, 2>(b128.n, s, gdev, rows);
-                brick_launch<R, 1, true, 128, 2>(b128.n, s, gdev, rows);
-                break;
-            default:
-                brick_launch<R, 0, false, 128, 4>(b128.n, s, gdev, rows);
-                brick_launch<R, 1, true, 128, 4>(b128.n, s, gdev, rows);
-                break;
+            case 64004: SEEDCG_BRICK(64, 4, b64) break;
+            case 64008: SEEDCG_BRICK(64, 8, b64) break;
+            case 128002: SEEDCG_BRICK(128, 2, b128) break;
+            default: SEEDCG_BRICK(128, 4, b128) break;
         }
+#undef SEEDCG_BRICK
     } else {
-        launch_mf<R>(code, 0, tiles, s, gdev, ng, rows);
-        launch_mf<R>(code, 1, tiles, s, gdev, ng, rows);
+        launch_mf<R>(code, 0, tiles, s, gdev, ng, rows, C);
+        alpha();
+        launch_mf<R>(code, 1, tiles, s, gdev, ng, rows, C);
     }
 }
 
@@ -667,7 +697,7 @@ std::vector<std::pair<std::string, int>>& tune_table() {
 
 template <typename R>
 int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const Brk& b64, const Brk& b128,
-                 const GroupDev<R>* gdev, int ng, Rows rows, cudaStream_t st) {
+                 const GroupDev<R>* gdev, int ng, Rows rows, const CgS& C, cudaStream_t st) {
     const std::string key = tune_key(groups, sizeof(R) == 8);
     {
         std::lock_guard<std::mutex> lk(tune_mutex());
@@ -686,9 +716,11 @@ int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const Brk& b64, 
     int best = 8;
     float best_ms = 1e30f;
     for (int c : cands) {
-        launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows);  // warm-up
+        // alpha is zero here: the D^dag kernel rewrites r unchanged, as it would for a
+        // stopped system, so the candidates are timed on the whole of steps 1 and 3
+        launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows, C, false);  // warm-up
         SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
-        for (int r = 0; r < 3; r++) launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows);
+        for (int r = 0; r < 3; r++) launch_op<R>(eo, c, tiles, b64, b128, st, gdev, ng, rows, C, false);
         SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -754,11 +786,12 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
     for (auto& gr : groups) {
         const long n = 12L * nsites(gr);
-        for (int k = 0; k < (eo ? 6 : 5); k++) add((size_t)gr.nsys * n * cxR);
+        for (int k = 0; k < (eo ? 5 : 4); k++) add((size_t)gr.nsys * n * cxR);   // x_R, r, p, t (+ e)
         for (int k = 0; k < 2; k++) add((size_t)gr.nsys * n * sizeof(double2));
         add((size_t)std::max(gr.nsys, 2) * n * sizeof(double2));
-        add((size_t)gr.nsys * ((nsites(gr) + TS - 1) / TS) * sizeof(double));
+        for (int k = 0; k < 2; k++) add((size_t)gr.nsys * ((nsites(gr) + TS - 1) / TS) * sizeof(double));
     }
+    add(sizeof(int) * 2 * kMaxGroups);
     add(sizeof(GroupDev<R>) * kMaxGroups);
     add(sizeof(double) * 8 * rows_cap + sizeof(int) * 8 * rows_cap);
     const size_t part_doubles = (size_t)rblocks * (rows_cap + 2) * 2 + 4096;
@@ -781,7 +814,6 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
         gd[f].xr = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].r = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].p = cv.take<cx_t<R>>((size_t)ns * n);
-        gd[f].q = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].t = cv.take<cx_t<R>>((size_t)ns * n);
         gd[f].e = eo ? cv.take<cx_t<R>>((size_t)ns * n) : nullptr;
         Gx[f] = cv.take<double2>((size_t)ns * n);
@@ -790,9 +822,13 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
         gd[f].ntiles = (nsites(groups[f]) + TS - 1) / TS;
         gd[f].b64 = (ng == 1 && !eo) ? brick_for(h->g, 64) : Brk{};
         gd[f].b128 = (ng == 1 && !eo) ? brick_for(h->g, 128) : Brk{};
-        if (std::max(gd[f].b64.n, gd[f].b128.n) > gd[f].ntiles)
-            throw Error{SEEDCG_ERR_ARG, "internal: more bricks than site tiles"};
+        // the brick kernels write one share per warp of 32 sites: the bricks must tile
+        // the lattice exactly, so that their warps are the ntiles site tiles
+        if ((gd[f].b64.n && gd[f].b64.n * 2 != gd[f].ntiles) ||
+            (gd[f].b128.n && gd[f].b128.n * 4 != gd[f].ntiles))
+            throw Error{SEEDCG_ERR_ARG, "internal: bricks do not tile the lattice"};
         gd[f].part = cv.take<double>((size_t)ns * gd[f].ntiles);
+        gd[f].part2 = cv.take<double>((size_t)ns * gd[f].ntiles);
         gd[f].tile0 = tile0;
         tile0 += gd[f].ntiles;
         SEEDCG_CUDA_TRY(cudaMemsetAsync(gd[f].xr, 0, (size_t)ns * n * cxR, st));
@@ -812,6 +848,7 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     rows.group = cv.take<int>(rows_cap);
     rows.local = cv.take<int>(rows_cap);
     rows.nact = cv.take<int>(kMaxGroups);
+    rows.first = cv.take<int>(kMaxGroups);
     int* ru_row = cv.take<int>(rows_cap);
     int* ru_slot = cv.take<int>(rows_cap);
     int* ru_sys = cv.take<int>(rows_cap);
@@ -820,9 +857,11 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     C.tol = tol;
     C.delta2 = reliable_delta > 0.0 ? reliable_delta * reliable_delta : 0.0;
     C.maxiter = maxiter;
+    C.rows_cap = rows_cap;
     SEEDCG_CUDA_TRY(cudaMemsetAsync(C.counters, 0, sizeof(unsigned) * (rows_cap + 64), st));
     SEEDCG_CUDA_TRY(cudaMemsetAsync(C.iters, 0, sizeof(int) * rows_cap, st));
     SEEDCG_CUDA_TRY(cudaMemsetAsync(C.flag, 0, sizeof(int) * rows_cap, st));
+    SEEDCG_CUDA_TRY(cudaMemsetAsync(C.alpha, 0, sizeof(double) * rows_cap, st));   // the autotuner's runs
     SEEDCG_CUDA_TRY(cudaMemcpyAsync(gdev, gd.data(), sizeof(GroupDev<R>) * ng, cudaMemcpyHostToDevice, st));
 
     // pinned host scratch (ints)
@@ -846,10 +885,11 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     std::vector<int> row0(ng);
     auto upload_rows = [&]() {
         // rows in group order, slots 0..nact-1 of each group
-        std::vector<int> rg(rows_cap, -1), rl(rows_cap, 0), na(kMaxGroups, 0);
+        std::vector<int> rg(rows_cap, -1), rl(rows_cap, 0), na(kMaxGroups, 0), fr(kMaxGroups, 0);
         int r = 0;
         for (int f = 0; f < ng; f++) {
             row0[f] = r;
+            fr[f] = r;
             na[f] = (int)sysmap[f].size();
             for (int l = 0; l < na[f]; l++, r++) {
                 rg[r] = f;
@@ -859,6 +899,7 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.group, rg.data(), sizeof(int) * rows_cap, cudaMemcpyHostToDevice, st));
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.local, rl.data(), sizeof(int) * rows_cap, cudaMemcpyHostToDevice, st));
         SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.nact, na.data(), sizeof(int) * kMaxGroups, cudaMemcpyHostToDevice, st));
+        SEEDCG_CUDA_TRY(cudaMemcpyAsync(rows.first, fr.data(), sizeof(int) * kMaxGroups, cudaMemcpyHostToDevice, st));
         SEEDCG_CUDA_TRY(cudaStreamSynchronize(st));
         return r;
     };
@@ -986,22 +1027,14 @@ void batched_cg(std::vector<CgGroup>& groups, double tol, double reliable_delta,
     // ---- the iteration chunk (graph-captured) ----
     const int gx = rblocks;
     const Brk b64 = gd[0].b64, b128 = gd[0].b128;
-    const int rpb = nrows > 0 ? autotune_rpb<R>(groups, tiles, b64, b128, gdev, ng, rows, st) : 8;
+    const int rpb = nrows > 0 ? autotune_rpb<R>(groups, tiles, b64, b128, gdev, ng, rows, C, st) : 8;
     out.rpb = rpb;
-    if (is_brick_code(rpb)) {
-        // the step-length shares now come from one entry per brick
-        gd[0].ntiles = rpb / 1000 == 64 ? b64.n : b128.n;
-        SEEDCG_CUDA_TRY(cudaMemcpyAsync(gdev, gd.data(), sizeof(GroupDev<R>), cudaMemcpyHostToDevice, st));
-    }
     auto chunk = [&](cudaStream_t s) {
         for (int it = 0; it < poll; it++) {
-            launch_op<R>(eo, rpb, tiles, b64, b128, s, gdev, ng, rows);
-            k_mf_alpha<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
+            launch_op<R>(eo, rpb, tiles, b64, b128, s, gdev, ng, rows, C, true);   // steps 1-3
+            k_mf_beta<R><<<rows_cap, 256, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
-            dim3 gr(gx, rows_cap);
-            k_mf_r<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
-            SEEDCG_CHECK_LAUNCH();
-            k_mf_xp<R><<<gr, kRedThreads, 0, s>>>(gdev, rows, C);
+            k_mf_xp<R><<<dim3(gx, rows_cap), kRedThreads, 0, s>>>(gdev, rows, C);
             SEEDCG_CHECK_LAUNCH();
         }
     };

@@ -177,12 +177,10 @@ struct Brick {
 
 // PIPE: at most 256 threads and up to 128 registers per thread, spent on
 // keeping more neighbour spinors in flight (wilson_site_prescaled_pipe)
-template <typename R, int DAG, int TB, bool DOT = false, bool PIPE = false>
+template <typename R, int DAG, int TB, bool PIPE = false>
 __global__ void __launch_bounds__(PIPE ? 256 : 384, (sizeof(R) == 4 ? 2 : 1))
 k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
-               const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out,
-               const cx_t<R>* __restrict__ pdot = nullptr, double* __restrict__ part = nullptr) {
-    __shared__ double sdot_w[12];
+               const cx_t<R>* __restrict__ in, cx_t<R>* __restrict__ out) {
     extern __shared__ unsigned char smem_raw[];
     cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);            // [2][4][9][TB]
     int* ss = reinterpret_cast<int*>(sl + 72 * TB);                  // [TB] site index
@@ -221,60 +219,16 @@ k_dslash_brick(Geom g, Brick br, const cx_t<R>* __restrict__ u, R kappa, int n,
     Nbr nb = neighbours(g, s);
     auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TB + j]; };
     auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TB + j]; };
-    if constexpr (!DOT) {
-        for (int r = q; r < n; r += rpb) {
-            const cx_t<R>* inr = in + (size_t)r * 12 * vol;
-            cx_t<R>* outr = out + (size_t)r * 12 * vol;
-            Spinor<R> res;
-            auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
-            if constexpr (PIPE)
-                wilson_site_prescaled_pipe<DAG, R>(nb, s, load, fl, bl, res);
-            else
-                wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
-            store_spinor(outr, vol, s, res);
-        }
-        return;
-    }
-    const int passes = (n + rpb - 1) / rpb;
-    for (int pass = 0; pass < passes; pass++) {
-        const int r = pass * rpb + q;
-        R dr = 0;
-        if (r < n) {
-            const cx_t<R>* inr = in + (size_t)r * 12 * vol;
-            cx_t<R>* outr = out + (size_t)r * 12 * vol;
-            Spinor<R> res;
-            auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
-            if constexpr (PIPE)
-                wilson_site_prescaled_pipe<DAG, R>(nb, s, load, fl, bl, res);
-            else
-                wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
-            store_spinor(outr, vol, s, res);
-            if (DOT) {
-                // Re p^dag (this result) at this site, for the CG step length
-                const cx_t<R>* pr = pdot + (size_t)r * 12 * vol;
-                R acc = 0;
-#pragma unroll
-                for (int k = 0; k < 12; k++) {
-                    const cx_t<R> pz = __ldg(pr + sidx(k, s, vol));
-                    const cx_t<R> rz = res.c[k / 3][k % 3];
-                    acc += pz.x * rz.x + pz.y * rz.y;
-                }
-                dr = acc;
-            }
-        }
-        if (DOT) {
-            // TB threads (TB/32 whole warps) share r: warp sums in the working
-            // precision, then a fixed-order FP64 sum over the warps
-            const double d = (double)warp_sum_t(dr);
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) sdot_w[threadIdx.x >> 5] = d;
-            __syncthreads();
-            if (threadIdx.x < rpb && pass * rpb + (int)threadIdx.x < n) {
-                double tsum = 0.0;
-                for (int w = 0; w < TB / 32; w++) tsum += sdot_w[threadIdx.x * (TB / 32) + w];
-                part[(size_t)(pass * rpb + threadIdx.x) * gridDim.x + blockIdx.x] = tsum;
-            }
-        }
+    for (int r = q; r < n; r += rpb) {
+        const cx_t<R>* inr = in + (size_t)r * 12 * vol;
+        cx_t<R>* outr = out + (size_t)r * 12 * vol;
+        Spinor<R> res;
+        auto load = [&](int y, Spinor<R>& p) { load_spinor(inr, vol, y, p); };
+        if constexpr (PIPE)
+            wilson_site_prescaled_pipe<DAG, R>(nb, s, load, fl, bl, res);
+        else
+            wilson_site_prescaled<DAG, R>(nb, s, load, fl, bl, res);
+        store_spinor(outr, vol, s, res);
     }
 }
 
@@ -298,18 +252,16 @@ bool make_brick(const Geom& g, Brick& br, int cap = 128) {
 
 // one launch of a brick kernel; the dynamic shared memory limit is raised once
 // per instantiation (each has its own static flag)
-template <typename R, int DAG, int TB, bool DOT, bool PIPE = false>
+template <typename R, int DAG, int TB, bool PIPE = false>
 void brick_go(int nb, int threads, size_t smem, cudaStream_t st, const Geom& g, const Brick& br,
-              const cx_t<R>* u, R kappa, int n, const cx_t<R>* in, cx_t<R>* out,
-              const cx_t<R>* pdot, double* part) {
+              const cx_t<R>* u, R kappa, int n, const cx_t<R>* in, cx_t<R>* out) {
     static bool attr = false;
     if (!attr) {
-        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_dslash_brick<R, DAG, TB, DOT, PIPE>,
+        SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_dslash_brick<R, DAG, TB, PIPE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         attr = true;
     }
-    k_dslash_brick<R, DAG, TB, DOT, PIPE><<<nb, threads, smem, st>>>(g, br, u, kappa, n, in, out, pdot,
-                                                                     part);
+    k_dslash_brick<R, DAG, TB, PIPE><<<nb, threads, smem, st>>>(g, br, u, kappa, n, in, out);
     SEEDCG_CHECK_LAUNCH();
 }
 
@@ -339,8 +291,7 @@ struct BrickChoice {
 template <typename R>
 void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n,
                         const cx_t<R>* in, cx_t<R>* out, cudaStream_t st,
-                        const cx_t<R>* pdot = nullptr, double* part = nullptr,
-                        int* nblocks_out = nullptr, const BrickChoice* force = nullptr);
+                        const BrickChoice* force = nullptr);
 
 template <typename R>
 BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n, const cx_t<R>* in,
@@ -383,10 +334,10 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
     for (const BrickChoice& c : cands) {
         Brick br;
         if (!make_brick(g, br, c.cap) || !(br.tb == 64 || br.tb == 96 || br.tb == 128)) continue;
-        launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, nullptr, nullptr, nullptr, &c);
+        launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, &c);
         SEEDCG_CUDA_TRY(cudaEventRecord(a, st));
         for (int r = 0; r < 3; r++)
-            launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, nullptr, nullptr, nullptr, &c);
+            launch_dslash_mrhs<R>(g, u, kappa, dag, n, in, out, st, &c);
         SEEDCG_CUDA_TRY(cudaEventRecord(b, st));
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
@@ -416,13 +367,12 @@ BrickChoice tuned_brick(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
 template <typename R>
 void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n,
                         const cx_t<R>* in, cx_t<R>* out, cudaStream_t st,
-                        const cx_t<R>* pdot, double* part, int* nblocks_out,
                         const BrickChoice* force) {
     if (n <= 0) return;
     Brick br;
     BrickChoice ch{128, 0, 0};
     if (force) ch = *force;
-    else if (!pdot) ch = tuned_brick<R>(g, u, kappa, dag, n, in, out, st);
+    else ch = tuned_brick<R>(g, u, kappa, dag, n, in, out, st);
     if (make_brick(g, br, ch.cap) && (br.tb == 64 || br.tb == 96 || br.tb == 128)) {
         const int maxr = (ch.pipe ? 256 : 384) / br.tb;
         const int passes = (n + maxr - 1) / maxr;
@@ -430,33 +380,24 @@ void launch_dslash_mrhs(const Geom& g, const cx_t<R>* u, R kappa, int dag, int n
         const int threads = br.tb * rpb;
         const size_t smem = (size_t)br.tb * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
         const int nb = br.ny * br.nz * g.L[3];
-        if (pdot) {
-            if (!dag) throw Error{SEEDCG_ERR_ARG, "fused dot only on the D^dag half"};
-            if (br.tb == 128) brick_go<R, 1, 128, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else if (br.tb == 96) brick_go<R, 1, 96, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 1, 64, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            if (nblocks_out) *nblocks_out = nb;
-            return;
-        }
         if (ch.pipe && br.tb == 128) {
-            if (dag) brick_go<R, 1, 128, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 0, 128, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (dag) brick_go<R, 1, 128, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
+            else brick_go<R, 0, 128, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
         } else if (ch.pipe && br.tb == 64) {
-            if (dag) brick_go<R, 1, 64, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 0, 64, false, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (dag) brick_go<R, 1, 64, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
+            else brick_go<R, 0, 64, true>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
         } else if (br.tb == 128) {
-            if (dag) brick_go<R, 1, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 0, 128, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (dag) brick_go<R, 1, 128>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
+            else brick_go<R, 0, 128>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
         } else if (br.tb == 96) {
-            if (dag) brick_go<R, 1, 96, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 0, 96, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (dag) brick_go<R, 1, 96>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
+            else brick_go<R, 0, 96>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
         } else {
-            if (dag) brick_go<R, 1, 64, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
-            else brick_go<R, 0, 64, false>(nb, threads, smem, st, g, br, u, kappa, n, in, out, pdot, part);
+            if (dag) brick_go<R, 1, 64>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
+            else brick_go<R, 0, 64>(nb, threads, smem, st, g, br, u, kappa, n, in, out);
         }
         return;
     }
-    if (pdot) throw Error{SEEDCG_ERR_ARG, "fused dot needs a brick-tiled lattice"};
     constexpr int TS = 32;
     // right-hand sides handled side by side per block: balanced passes of <= 12
     const int passes = (n + 11) / 12;
@@ -521,29 +462,11 @@ void dslash_mrhs_f32(const Geom& g, const float2* u, float kappa, int dag, int n
 void dslash_mrhs_fixed_f64(const Geom& g, const double2* u, double kappa, int dag, int n,
                            const double2* in, double2* out, cudaStream_t s) {
     const BrickChoice c{128, 0};
-    launch_dslash_mrhs<double>(g, u, kappa, dag, n, in, out, s, nullptr, nullptr, nullptr, &c);
+    launch_dslash_mrhs<double>(g, u, kappa, dag, n, in, out, s, &c);
 }
 void dslash_mrhs_fixed_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                            const float2* in, float2* out, cudaStream_t s) {
     const BrickChoice c{128, 0};
-    launch_dslash_mrhs<float>(g, u, kappa, dag, n, in, out, s, nullptr, nullptr, nullptr, &c);
+    launch_dslash_mrhs<float>(g, u, kappa, dag, n, in, out, s, &c);
 }
-bool dslash_dot_supported(const Geom& g) {
-    Brick br;
-    return make_brick(g, br) && (br.tb == 64 || br.tb == 96 || br.tb == 128);
-}
-int dslash_dot_blocks(const Geom& g) {
-    Brick br;
-    make_brick(g, br);
-    return br.ny * br.nz * g.L[3];
-}
-void dslash_mrhs_dot_f64(const Geom& g, const double2* u, double kappa, int n, const double2* in,
-                         double2* out, const double2* p, double* part, cudaStream_t s) {
-    launch_dslash_mrhs<double>(g, u, kappa, 1, n, in, out, s, p, part);
-}
-void dslash_mrhs_dot_f32(const Geom& g, const float2* u, float kappa, int n, const float2* in,
-                         float2* out, const float2* p, double* part, cudaStream_t s) {
-    launch_dslash_mrhs<float>(g, u, kappa, 1, n, in, out, s, p, part);
-}
-
 }  // namespace seedcg

@@ -182,13 +182,4 @@ void dslash_mrhs_fixed_f64(const Geom& g, const double2* u, double kappa, int da
 void dslash_mrhs_fixed_f32(const Geom& g, const float2* u, float kappa, int dag, int n,
                            const float2* in, float2* out, cudaStream_t s);
 
-// D^dag on n fields fused with the CG step-length dot: part[r][b] receives block
-// b's share of Re p_r^dag (D^dag in_r); needs a brick-tiled lattice
-bool dslash_dot_supported(const Geom& g);
-int dslash_dot_blocks(const Geom& g);
-void dslash_mrhs_dot_f64(const Geom& g, const double2* u, double kappa, int n, const double2* in,
-                         double2* out, const double2* p, double* part, cudaStream_t s);
-void dslash_mrhs_dot_f32(const Geom& g, const float2* u, float kappa, int n, const float2* in,
-                         float2* out, const float2* p, double* part, cudaStream_t s);
-
 }  // namespace seedcg

@@ -44,6 +44,12 @@ inline int vec_blocks(long n, int w) {
 
 inline int site_blocks(int vol) { return (vol + kRedThreads - 1) / kRedThreads; }
 
+// blocks for a streaming pass that ends in one grid reduction: two per SM.  Every
+// block takes the reduction's atomic ticket, and thousands of tickets on one
+// counter cost more than the pass's loads (the 16^3x32 Lanczos update: 23 us at
+// 304 blocks against 35 us at 3072)
+inline int lean_blocks(long n, int w) { return std::min(vec_blocks(n, w), 2 * 152); }
+
 // ===========================================================================
 // phase A kernels.  Every kernel of iteration i returns at once when i
 // exceeds the current target m (uniformly for the whole grid), so the host
@@ -314,6 +320,12 @@ k_lz_update_v(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* _
     const long ng = n / W;
     for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < ng; g += (long)gridDim.x * blockDim.x) {
         cx_t<R> vv[W], fv[W], ww[W];
+        double2 xv[W];
+        if (X1) {
+            // issued first: the FP64 x^1 is the widest stream of the pass
+#pragma unroll
+            for (int k = 0; k < W; k++) xv[k] = __ldcs(x1 + g * W + k);
+        }
         if constexpr (W == 2) {
             const float4 a4 = reinterpret_cast<const float4*>(v)[g];
             const float4 b4 = reinterpret_cast<const float4*>(f)[g];
@@ -350,10 +362,9 @@ k_lz_update_v(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* _
         if (X1) {
 #pragma unroll
             for (int k = 0; k < W; k++) {
-                double2 xv = __ldcs(x1 + g * W + k);
-                xv.x = fma(zt, (double)ww[k].x, xv.x);
-                xv.y = fma(zt, (double)ww[k].y, xv.y);
-                __stcs(x1 + g * W + k, xv);
+                xv[k].x = fma(zt, (double)ww[k].x, xv[k].x);
+                xv[k].y = fma(zt, (double)ww[k].y, xv[k].y);
+                __stcs(x1 + g * W + k, xv[k]);
             }
         }
     }
@@ -929,7 +940,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
                 k_lz_update<R, true><<<rb, kRedThreads, 0, st>>>(
                     v, fv, wv, reinterpret_cast<cx_t<R>*>(X64), nrhs, n, i, po_now ? 0 : 1, L);
             else
-                k_lz_update_v<R, true><<<vec_blocks(n, 16 / (int)sizeof(cx_t<R>)), kRedThreads, 0, st>>>(
+                k_lz_update_v<R, true><<<lean_blocks(n, 16 / (int)sizeof(cx_t<R>)), kRedThreads, 0, st>>>(
                     v, fv, wv, X64, n, i, po_now ? 0 : 1, L);
             SEEDCG_CHECK_LAUNCH();
             if (po_now) {

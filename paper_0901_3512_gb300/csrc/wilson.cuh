@@ -69,6 +69,18 @@ __device__ __forceinline__ void spin_accum(Spinor<R>& acc, const cx_t<R> r[2][3]
     }
 }
 
+// ||v||^2 at one site, in the working precision
+template <typename R>
+__device__ __forceinline__ R spinor_norm2(const Spinor<R>& v) {
+    R a = 0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const cx_t<R> z = v.c[k / 3][k % 3];
+        a += z.x * z.x + z.y * z.y;
+    }
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // spinor loads/stores in the internal layouts
 // ---------------------------------------------------------------------------
@@ -95,6 +107,20 @@ __device__ __forceinline__ void store_spinor(float2* __restrict__ p, int vol, in
         const float2 a = v.c[(2 * c) / 3][(2 * c) % 3], b = v.c[(2 * c + 1) / 3][(2 * c + 1) % 3];
         q[(size_t)c * vol] = make_float4(a.x, a.y, b.x, b.y);
     }
+}
+// coherent loads, for a field that the same kernel writes back at the same site
+__device__ __forceinline__ void load_spinor_rw(const float2* p, int vol, int s, Spinor<float>& out) {
+    const float4* q = reinterpret_cast<const float4*>(p) + s;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        const float4 z = q[(size_t)c * vol];
+        out.c[(2 * c) / 3][(2 * c) % 3] = make_float2(z.x, z.y);
+        out.c[(2 * c + 1) / 3][(2 * c + 1) % 3] = make_float2(z.z, z.w);
+    }
+}
+__device__ __forceinline__ void load_spinor_rw(const double2* p, int vol, int s, Spinor<double>& out) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) out.c[k / 3][k % 3] = p[sidx(k, s, vol)];
 }
 __device__ __forceinline__ void load_spinor(const double2* __restrict__ p, int vol, int s,
                                             Spinor<double>& out) {

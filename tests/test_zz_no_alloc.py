@@ -14,9 +14,16 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("prec,multi,tol", [(0, 1, 1e-13), (0, 0, 1e-13), (1, 1, 1e-5), (1, 0, 1e-5)])
 def test_noalloc_apply_matches_apply(prec, multi, tol):
+    """Against seedcg_apply and against the oracle's C operator (D, D^dag and
+    M = D^dag D of Section 3), in norm and element by element (max-abs relative to
+    the largest entry)."""
     need_gpu()
+    from oracle.wilson import WilsonOperator
     dims = (4, 4, 4, 8)
-    s = seedcg.Solver(dims, W.gauge_field(dims, 0.5, 31), 0.2)
+    u = W.gauge_field(dims, 0.5, 31)
+    s = seedcg.Solver(dims, u, 0.2)
+    op_or = WilsonOperator(dims, u, 0.2)
+    apply_or = {seedcg.OP_D: op_or.D, seedcg.OP_DDAG: op_or.Ddag, seedcg.OP_M: op_or.M}
     for call in range(2):  # two calls in a row share the fixed scratch
         x = W.random_spinors(dims, 3, 40 + call)
         xd = dev(x)
@@ -25,7 +32,11 @@ def test_noalloc_apply_matches_apply(prec, multi, tol):
             got = dev(np.zeros_like(x))
             seedcg.seedcg_apply(s.h, op, prec, multi, 3, xd, want)
             seedcg.seedcg_apply_noalloc(s.h, op, prec, multi, 3, xd, got)
-            assert rel(host(got), host(want)) <= tol
+            g = host(got)
+            assert rel(g, host(want)) <= tol
+            ref = np.stack([apply_or[op](x[j]) for j in range(3)])
+            assert rel(g, ref) <= tol
+            assert np.max(np.abs(g - ref)) <= tol * np.max(np.abs(ref))
     s.close()
 
 
