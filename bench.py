@@ -93,10 +93,11 @@ def _args():
                    help="the even-odd preconditioned system of Section 3 (A^dag A x_o = A^dag phi on "
                         "odd-site half vectors) on the same workload: its own JSON line with its PO "
                         "roofline, beside one full-lattice solve of the same sources (not a bench line)")
-    p.add_argument("--only", default=None, choices=["dslash", "po", "guess"],
+    p.add_argument("--only", default=None, choices=["dslash", "po", "guess", "cg"],
                    help="profiling aid: run only the 12-RHS dslash timing, one solve capped "
-                        "at --m-max Lanczos iterations (re-orthogonalisation kernels), or --steps "
-                        "forward passes of the learned guess on the workload's field")
+                        "at --m-max Lanczos iterations (re-orthogonalisation kernels), --steps "
+                        "forward passes of the learned guess, or the workload's systems by "
+                        "batched CG from zero (no stored basis: a few GB on the device)")
     return p.parse_args()
 
 
@@ -794,6 +795,19 @@ def run_only(args):
         e1.record()
         torch.cuda.synchronize()
         print(json.dumps({"only": "guess", "ms_per_forward": e0.elapsed_time(e1) / max(args.steps, 1)}))
+    elif args.only == "cg":
+        eta = torch.from_numpy(wl.sources_for(0)).cuda()
+        B = torch.empty_like(eta)
+        s.apply(seedcg.OP_DDAG, eta, B, prec=0, multi=1)
+        X = torch.zeros_like(B)
+        s.set_options(precision=prec, past_factor=wl.past_factor, m_max=args.m_max, seed_mode=3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        code, info = s.solve(B, X, wl.tol, 0, wl.reorth_period, allow_not_converged=True)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"only": "cg", "status": code, "seconds": e0.elapsed_time(e1) / 1000.0,
+                          "iters": info["iters"], "max_true_resid": max(info["true_resid"])}))
     else:
         eta = torch.from_numpy(wl.sources_for(0)).cuda()
         B = torch.empty_like(eta)

@@ -715,6 +715,7 @@ int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const Brk& b64, 
     SEEDCG_CUDA_TRY(cudaEventCreate(&b));
     int best = 8;
     float best_ms = 1e30f;
+    const bool tune_log = getenv("SEEDCG_TUNE_LOG") != nullptr;
     for (int c : cands) {
         // alpha is zero here: the D^dag kernel rewrites r unchanged, as it would for a
         // stopped system, so the candidates are timed on the whole of steps 1 and 3
@@ -725,6 +726,7 @@ int autotune_rpb(const std::vector<CgGroup>& groups, int tiles, const Brk& b64, 
         SEEDCG_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0.f;
         SEEDCG_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (tune_log) fprintf(stderr, "seedcg tune %s: code %d: %.4f ms\n", key.c_str(), c, ms / 3);
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
