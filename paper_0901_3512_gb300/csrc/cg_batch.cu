@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? (RPB <= 8 ? 3 : 2)
 k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     __shared__ cx_t<R> sl[2][4][9][TS];
     __shared__ int sb[4][TS];
+    __shared__ Nbr snb[TS];   // neighbours of the tile's sites (kept out of the registers)
     __shared__ R sgn[2][TS];
     __shared__ int s_tile0[kMaxGroups];
     if (threadIdx.x < ng) s_tile0[threadIdx.x] = G[threadIdx.x].tile0;
@@ -152,6 +153,7 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
         const int s = s0 + threadIdx.x;
         if (s < vol) {
             Nbr nb = neighbours(g, s);
+            snb[threadIdx.x] = nb;
 #pragma unroll
             for (int mu = 0; mu < 4; mu++) sb[mu][threadIdx.x] = nb.b[mu];
             sgn[0][threadIdx.x] = nb.fwrap_t ? kappa : -kappa;
@@ -177,8 +179,7 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     const int qg = threadIdx.x / TS;  // warp = right-hand-side group
     const int s = s0 + j;
     const bool live = s < vol;
-    Nbr nb;
-    if (live) nb = neighbours(g, s);
+    const Nbr& nb = snb[j];
     auto fl = [&](int mu, int e) { return sl[0][mu][e][j]; };
     auto bl = [&](int mu, int e) { return sl[1][mu][e][j]; };
     const cx_t<R>* in = DAG ? gd.t : gd.p;
@@ -192,8 +193,8 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
             if (DAG) {
                 dr = r_update_site(gd.r + (size_t)r * gd.n, vol, s, res, (R)C.alpha[rows.first[f] + r]);
             } else {
+                dr = spinor_norm2(res);   // before the store: fewer live registers
                 store_spinor(gd.t + (size_t)r * gd.n, vol, s, res);
-                dr = spinor_norm2(res);
             }
         }
         put_share(DAG ? gd.part2 : gd.part, gd.ntiles, r, tile, dr);
@@ -204,11 +205,19 @@ k_mf_dslash(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
 // every active system of every field (tiles of TS odd / even half sites):
 //   STAGE 0  e = H_eo p;  1  t = p - kappa^2 H_oe e = A p, and ||A p||^2 = p^dag M p;
 //   STAGE 2  e = H^dag_eo t;  3  q = t - kappa^2 H^dag_oe e, r -= alpha q and ||r||^2
+// The tile's links (U_mu(x) and U_mu(x - mu) of its 32 sites of the output parity) are
+// staged once in shared memory, times the hop coefficient (1, or -kappa^2 in stages 1
+// and 3) and the t-boundary sign, and reused by every system of the tile.
 template <typename R, int STAGE, int RPB>
 __global__ void __launch_bounds__(TS * RPB, (sizeof(R) == 4 ? 2 : 1))
 k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     constexpr int DAG = STAGE >= 2 ? 1 : 0;
     constexpr int POUT = (STAGE & 1) ? 1 : 0;
+    __shared__ cx_t<R> sl[2][4][9][TS];
+    __shared__ int ssite[TS];
+    __shared__ int sb[4][TS];                 // x - mu (full site)
+    __shared__ Nbr snb[TS];                   // neighbours of the tile's sites
+    __shared__ R sgn[2][TS];
     __shared__ int s_tile0[kMaxGroups];
     if (threadIdx.x < ng) s_tile0[threadIdx.x] = G[threadIdx.x].tile0;
     __syncthreads();
@@ -217,13 +226,44 @@ k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
     const int nsys = rows.nact[f];
     if (nsys == 0) return;
     const Geom g = gd.g;
-    const int vh = g.vol / 2;
+    const int vol = g.vol, vh = g.vol / 2;
     const int tile = blockIdx.x - gd.tile0;
+    const R kk = gd.kappa * gd.kappa;
+    const R chop = POUT ? -kk : R(1);
+    if (threadIdx.x < TS) {
+        const int h = tile * TS + threadIdx.x;
+        if (h < vh) {
+            const int s = eo_site(g, h, POUT);
+            const Nbr nb = neighbours(g, s);
+            ssite[threadIdx.x] = s;
+            snb[threadIdx.x] = nb;
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) sb[mu][threadIdx.x] = nb.b[mu];
+            sgn[0][threadIdx.x] = nb.fwrap_t ? -chop : chop;
+            sgn[1][threadIdx.x] = nb.bwrap_t ? -chop : chop;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 72 * TS; e += blockDim.x) {
+        const int j = e % TS;
+        const int c = (e / TS) % 9;
+        const int mu = (e / (9 * TS)) % 4;
+        const int dir = e / (36 * TS);
+        cx_t<R> z = mk<R>(0, 0);
+        if (tile * TS + j < vh) {
+            z = __ldg(gd.u + (size_t)(mu * 9 + c) * vol + (dir ? sb[mu][j] : ssite[j]));
+            z = cscale(z, mu == 3 ? sgn[dir][j] : chop);
+        }
+        sl[dir][mu][c][j] = z;
+    }
+    __syncthreads();
     const int j = threadIdx.x % TS;
     const int qg = threadIdx.x / TS;
     const int hh = tile * TS + j;
     const bool live = hh < vh;
-    const R kk = gd.kappa * gd.kappa;
+    const Nbr& nb = snb[j];
+    auto fl = [&](int mu, int e) { return sl[0][mu][e][j]; };
+    auto bl = [&](int mu, int e) { return sl[1][mu][e][j]; };
     const cx_t<R>* in = STAGE == 0 ? gd.p : STAGE == 2 ? gd.t : gd.e;
     const cx_t<R>* same = STAGE == 1 ? gd.p : STAGE == 3 ? gd.t : nullptr;
     cx_t<R>* out = (STAGE == 0 || STAGE == 2) ? gd.e : gd.t;   // STAGE 3 stores nothing
@@ -232,13 +272,18 @@ k_mf_eo(const GroupDev<R>* __restrict__ G, int ng, Rows rows, CgS C) {
         if (live) {
             const size_t off = (size_t)r * gd.n;
             Spinor<R> acc;
-            eo_site_apply<R, DAG>(g, gd.u, POUT, hh, in + off, POUT ? same + off : nullptr, R(1),
-                                  POUT ? -kk : R(1), acc);
+            if (POUT) {
+                load_spinor(same + off, vh, hh, acc);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; k++) acc.c[k / 3][k % 3] = mk<R>(0, 0);
+            }
+            eo_hops_prescaled<R, DAG>(nb, in + off, vh, fl, bl, acc);
             if (STAGE == 3) {
                 dr = r_update_site(gd.r + off, vh, hh, acc, (R)C.alpha[rows.first[f] + r]);
             } else {
-                store_spinor(out + off, vh, hh, acc);
                 if (STAGE == 1) dr = spinor_norm2(acc);
+                store_spinor(out + off, vh, hh, acc);
             }
         }
         if (STAGE == 1 || STAGE == 3) put_share(STAGE == 1 ? gd.part : gd.part2, gd.ntiles, r, tile, dr);
@@ -257,9 +302,9 @@ __global__ void __launch_bounds__(TB * RPB, (sizeof(R) == 4 && TB * RPB <= 256) 
 k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     extern __shared__ unsigned char smem_raw[];
     cx_t<R>* sl = reinterpret_cast<cx_t<R>*>(smem_raw);   // [2][4][9][TB]
-    int* ss = reinterpret_cast<int*>(sl + 72 * TB);         // [TB] site
-    int* sbk = ss + TB;                                     // [4][TB] x - mu
-    R* sg = reinterpret_cast<R*>(sbk + 4 * TB);             // [2][TB]
+    Nbr* snb = reinterpret_cast<Nbr*>(sl + 72 * TB);        // [TB] neighbours of the brick's sites
+    int* ss = reinterpret_cast<int*>(snb + TB);             // [TB] site
+    R* sg = reinterpret_cast<R*>(ss + TB);                  // [2][TB]
     const GroupDev<R>& gd = G[0];
     const int nsys = rows.nact[0];
     if (nsys == 0) return;
@@ -278,8 +323,7 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
         const int s = x + g.stride[1] * (iy * br.by + dy) + g.stride[2] * (iz * br.bz + dz) + g.stride[3] * t;
         ss[j] = s;
         const Nbr nb = neighbours(g, s);
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) sbk[mu * TB + j] = nb.b[mu];
+        snb[j] = nb;
         sg[j] = nb.fwrap_t ? kappa : -kappa;
         sg[TB + j] = nb.bwrap_t ? kappa : -kappa;
     }
@@ -289,7 +333,7 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
         const int c = (e / TB) % 9;
         const int mu = (e / (9 * TB)) % 4;
         const int dir = e / (36 * TB);
-        const cx_t<R> z = __ldg(gd.u + (size_t)(mu * 9 + c) * vol + (dir ? sbk[mu * TB + j] : ss[j]));
+        const cx_t<R> z = __ldg(gd.u + (size_t)(mu * 9 + c) * vol + (dir ? snb[j].b[mu] : ss[j]));
         sl[e] = cscale(z, mu == 3 ? sg[dir * TB + j] : -kappa);
     }
     __syncthreads();
@@ -297,7 +341,7 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     const int q = threadIdx.x / TB;
     const int s = ss[j];
     const int tile32 = blockIdx.x * (TB / 32) + (j >> 5);
-    const Nbr nb = neighbours(g, s);
+    const Nbr& nb = snb[j];
     auto fl = [&](int mu, int e) { return sl[((0 * 4 + mu) * 9 + e) * TB + j]; };
     auto bl = [&](int mu, int e) { return sl[((1 * 4 + mu) * 9 + e) * TB + j]; };
     const cx_t<R>* in = DAG ? gd.t : gd.p;
@@ -311,8 +355,8 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
         if (DAG) {
             dr = r_update_site(gd.r + (size_t)r * gd.n, vol, s, res, (R)C.alpha[rows.first[0] + r]);
         } else {
-            store_spinor(gd.t + (size_t)r * gd.n, vol, s, res);
             dr = spinor_norm2(res);
+            store_spinor(gd.t + (size_t)r * gd.n, vol, s, res);
         }
         put_share(DAG ? gd.part2 : gd.part, gd.ntiles, r, tile32, dr);
     }
@@ -579,7 +623,9 @@ void launch_mf_eo(int rpb, int stage, int tiles, cudaStream_t s, const GroupDev<
 
 template <typename R, int DAG, int TB, int RPB>
 void brick_launch(int nb, cudaStream_t s, const GroupDev<R>* gdev, Rows rows, const CgS& C) {
-    const size_t smem = (size_t)TB * (72 * sizeof(cx_t<R>) + 5 * sizeof(int) + 2 * sizeof(R));
+    const size_t smem = (size_t)TB * (72 * sizeof(cx_t<R>) + sizeof(Nbr) + sizeof(int) + 2 * sizeof(R));
+    static_assert(sizeof(Nbr) % 4 == 0 && (TB * (sizeof(Nbr) + sizeof(int))) % sizeof(R) == 0,
+                  "brick shared-memory layout alignment");
     static bool attr = false;
     if (!attr) {
         SEEDCG_CUDA_TRY(cudaFuncSetAttribute(k_mf_brick<R, DAG, TB, RPB>,

@@ -50,6 +50,31 @@ __device__ __forceinline__ void eo_hops(const Geom& g, const cx_t<R>* __restrict
 #undef SEEDCG_EO_HOP
 }
 
+// acc += (H other)(s) with links that already carry the hop coefficient and the
+// t-boundary sign (staged that way by the batched CG's tile kernels): no scaling.
+// Fwd(mu, e) / Bwd(mu, e) give element e = 3a+b of U_mu(s) / U_mu(s - mu).
+template <typename R, int DAG, typename Fwd, typename Bwd>
+__device__ __forceinline__ void eo_hops_prescaled(const Nbr& nb, const cx_t<R>* __restrict__ other, int vh,
+                                                  Fwd fl, Bwd bl, Spinor<R>& acc) {
+    constexpr int SF = DAG ? 1 : -1;
+    constexpr int SB = -SF;
+    Spinor<R> p;
+#define SEEDCG_EO_HOP_P(MU)                                                                          \
+    {                                                                                                \
+        auto lf = [&](int a, int b) { return fl(MU, 3 * a + b); };                                   \
+        auto lb = [&](int a, int b) { return bl(MU, 3 * a + b); };                                   \
+        load_spinor(other, vh, nb.f[MU] >> 1, p);                                                    \
+        hop<MU, SF, false, R, decltype(lf), false>(acc, p, lf, R(1));                                \
+        load_spinor(other, vh, nb.b[MU] >> 1, p);                                                    \
+        hop<MU, SB, true, R, decltype(lb), false>(acc, p, lb, R(1));                                 \
+    }
+    SEEDCG_EO_HOP_P(0)
+    SEEDCG_EO_HOP_P(1)
+    SEEDCG_EO_HOP_P(2)
+    SEEDCG_EO_HOP_P(3)
+#undef SEEDCG_EO_HOP_P
+}
+
 // out(h) = c_diag same(h) + c_hop (H other)(x), x the parity-p_out site of half index h
 // (same may be null: no diagonal term)
 template <typename R, int DAG>
