@@ -318,53 +318,67 @@ k_lz_update_v(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, cx_t<R>* _
     }
     R part = 0;
     const long ng = n / W;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < ng; g += (long)gridDim.x * blockDim.x) {
-        cx_t<R> vv[W], fv[W], ww[W];
-        double2 xv[W];
-        if (X1) {
-            // issued first: the FP64 x^1 is the widest stream of the pass
+    const long st = (long)gridDim.x * blockDim.x;
+    // two 16-byte groups per thread and trip, every load of both issued before the
+    // arithmetic: the grid is two blocks per SM, so each thread keeps more bytes in flight
+    for (long g0 = blockIdx.x * (long)blockDim.x + threadIdx.x; g0 < ng; g0 += 2 * st) {
+        const bool two = g0 + st < ng;
+        cx_t<R> vv[2][W], fv[2][W], ww[2][W];
+        double2 xv[2][W];
 #pragma unroll
-            for (int k = 0; k < W; k++) xv[k] = __ldcs(x1 + g * W + k);
-        }
-        if constexpr (W == 2) {
-            const float4 a4 = reinterpret_cast<const float4*>(v)[g];
-            const float4 b4 = reinterpret_cast<const float4*>(f)[g];
-            vv[0] = mk<R>(a4.x, a4.y); vv[1] = mk<R>(a4.z, a4.w);
-            fv[0] = mk<R>(b4.x, b4.y); fv[1] = mk<R>(b4.z, b4.w);
+        for (int h = 0; h < 2; h++) {
+            if (h == 1 && !two) break;
+            const long g = g0 + h * st;
             if (X1) {
-                const float4 c4 = i > 1 ? __ldcs(reinterpret_cast<const float4*>(w) + g) : make_float4(0, 0, 0, 0);
-                ww[0] = mk<R>(c4.x, c4.y); ww[1] = mk<R>(c4.z, c4.w);
+                // the FP64 x^1 is the widest stream of the pass
+#pragma unroll
+                for (int k = 0; k < W; k++) xv[h][k] = __ldcs(x1 + g * W + k);
             }
-        } else {
-            vv[0] = v[g];
-            fv[0] = f[g];
-            if (X1) ww[0] = i > 1 ? __ldcs(reinterpret_cast<const double2*>(w) + g) : mk<R>(0, 0);
+            if constexpr (W == 2) {
+                const float4 a4 = reinterpret_cast<const float4*>(v)[g];
+                const float4 b4 = reinterpret_cast<const float4*>(f)[g];
+                vv[h][0] = mk<R>(a4.x, a4.y); vv[h][1] = mk<R>(a4.z, a4.w);
+                fv[h][0] = mk<R>(b4.x, b4.y); fv[h][1] = mk<R>(b4.z, b4.w);
+                if (X1) {
+                    const float4 c4 = i > 1 ? __ldcs(reinterpret_cast<const float4*>(w) + g) : make_float4(0, 0, 0, 0);
+                    ww[h][0] = mk<R>(c4.x, c4.y); ww[h][1] = mk<R>(c4.z, c4.w);
+                }
+            } else {
+                vv[h][0] = v[g];
+                fv[h][0] = f[g];
+                if (X1) ww[h][0] = i > 1 ? __ldcs(reinterpret_cast<const double2*>(w) + g) : mk<R>(0, 0);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < W; k++) {
-            fv[k].x -= a * vv[k].x;
-            fv[k].y -= a * vv[k].y;
-            part += fv[k].x * fv[k].x + fv[k].y * fv[k].y;
-            if (X1) {
-                ww[k].x = (vv[k].x - bp * ww[k].x) * idl;
-                ww[k].y = (vv[k].y - bp * ww[k].y) * idl;
-            }
-        }
-        // w and x^1 are streamed (evict-first): each is touched once per iteration, and
-        // caching them would push the operator's links and vectors out of L2
-        if constexpr (W == 2) {
-            reinterpret_cast<float4*>(f)[g] = make_float4(fv[0].x, fv[0].y, fv[1].x, fv[1].y);
-            if (X1) __stcs(reinterpret_cast<float4*>(w) + g, make_float4(ww[0].x, ww[0].y, ww[1].x, ww[1].y));
-        } else {
-            f[g] = fv[0];
-            if (X1) __stcs(reinterpret_cast<double2*>(w) + g, make_double2(ww[0].x, ww[0].y));
-        }
-        if (X1) {
+        for (int h = 0; h < 2; h++) {
+            if (h == 1 && !two) break;
+            const long g = g0 + h * st;
 #pragma unroll
             for (int k = 0; k < W; k++) {
-                xv[k].x = fma(zt, (double)ww[k].x, xv[k].x);
-                xv[k].y = fma(zt, (double)ww[k].y, xv[k].y);
-                __stcs(x1 + g * W + k, xv[k]);
+                fv[h][k].x -= a * vv[h][k].x;
+                fv[h][k].y -= a * vv[h][k].y;
+                part += fv[h][k].x * fv[h][k].x + fv[h][k].y * fv[h][k].y;
+                if (X1) {
+                    ww[h][k].x = (vv[h][k].x - bp * ww[h][k].x) * idl;
+                    ww[h][k].y = (vv[h][k].y - bp * ww[h][k].y) * idl;
+                }
+            }
+            // w and x^1 are streamed (evict-first): each is touched once per iteration, and
+            // caching them would push the operator's links and vectors out of L2
+            if constexpr (W == 2) {
+                reinterpret_cast<float4*>(f)[g] = make_float4(fv[h][0].x, fv[h][0].y, fv[h][1].x, fv[h][1].y);
+                if (X1) __stcs(reinterpret_cast<float4*>(w) + g, make_float4(ww[h][0].x, ww[h][0].y, ww[h][1].x, ww[h][1].y));
+            } else {
+                f[g] = fv[h][0];
+                if (X1) __stcs(reinterpret_cast<double2*>(w) + g, make_double2(ww[h][0].x, ww[h][0].y));
+            }
+            if (X1) {
+#pragma unroll
+                for (int k = 0; k < W; k++) {
+                    xv[h][k].x = fma(zt, (double)ww[h][k].x, xv[h][k].x);
+                    xv[h][k].y = fma(zt, (double)ww[h][k].y, xv[h][k].y);
+                    __stcs(x1 + g * W + k, xv[h][k]);
+                }
             }
         }
     }
@@ -563,6 +577,7 @@ k_po_finish(const cx_t<R>* __restrict__ v, cx_t<R>* __restrict__ f, long n, int 
 }
 
 // Step 9: store v_i into V (storage type VT); v_{i+1} = f / beta_i
+// (FP32: a thread moves two complex entries, 16-byte loads of v and f)
 template <typename R, typename VT>
 __global__ void k_lz_advance(const cx_t<R>* __restrict__ v, const cx_t<R>* __restrict__ f,
                              cx_t<R>* __restrict__ vnext, VT* __restrict__ Vrow, long n, int i,
@@ -571,11 +586,24 @@ __global__ void k_lz_advance(const cx_t<R>* __restrict__ v, const cx_t<R>* __res
     const double b = L.beta[i - 1];
     const bool go = b > 0.0 && i < L.ctl->m;
     const R inv = go ? (R)(1.0 / b) : R(0);
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
-         e += (long)gridDim.x * blockDim.x) {
-        cx_t<R> vv = v[e];
-        st_cx(Vrow, e, vv);
-        if (go) vnext[e] = cscale(f[e], inv);
+    if constexpr (sizeof(R) == 4) {
+        const long ng = n / 2;   // n = 12 * sites is even
+        for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < ng;
+             g += (long)gridDim.x * blockDim.x) {
+            const float4 a = reinterpret_cast<const float4*>(v)[g];
+            float4 c;
+            if (go) c = reinterpret_cast<const float4*>(f)[g];
+            st_cx(Vrow, 2 * g, make_float2(a.x, a.y));
+            st_cx(Vrow, 2 * g + 1, make_float2(a.z, a.w));
+            if (go) reinterpret_cast<float4*>(vnext)[g] = make_float4(c.x * inv, c.y * inv, c.z * inv, c.w * inv);
+        }
+    } else {
+        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+             e += (long)gridDim.x * blockDim.x) {
+            cx_t<R> vv = v[e];
+            st_cx(Vrow, e, vv);
+            if (go) vnext[e] = cscale(f[e], inv);
+        }
     }
 }
 
