@@ -17,7 +17,9 @@ What is checked, all against the oracle or against mathematics:
     complex entries per row, > 2000 rows) equals the FP64 product of the
     same stored rows with the same vectors, element by element, on sampled
     rows (first and last rows, tile edges, random rows), within the bf16
-    rounding bound 2^-9 ||v_a|| ||x_j|| of the operand plus FP32 sums.
+    rounding bound 2^-9 ||v_a|| ||x_j|| of the operand plus FP32 sums;
+  * the even-odd system of Section 3 on the same sources: A^dag A residuals
+    by the oracle's even-odd operator, D x = eta residuals by its plain-C D.
 """
 import math
 
@@ -148,3 +150,48 @@ def test_headline_matches_plain_fp64_gpu_solve(headline):
     # the rounding of the bf16 basis and FP32 vectors (reported, loosely held)
     assert abs(info_mixed["m_conv"] - info["m_conv"]) <= math.ceil(0.1 * info["m_conv"])
     print(f"m_conv mixed {info_mixed['m_conv']} FP64 {info['m_conv']}; FP64 iters {info['iters']}")
+
+
+def test_even_odd_16x16x16x32_bf16_by_the_oracle():
+    """Section 3's even-odd system at the benchmark's size and in the launch
+    configuration its `even_odd` line times (twelve point sources, bf16 basis,
+    tcgen05 seed projection, k = 10, 2x past convergence): every residual of
+    A^dag A x_o = A^dag phi recomputed with the oracle's even-odd operator meets
+    tol; the reconstructed solution's residual of D x = eta recomputed with the
+    oracle's plain-C D equals the reported one; and the Krylov dimension at
+    convergence is below the full-lattice system's (the better conditioning of
+    the Schur complement)."""
+    need_gpu()
+    import torch
+    from oracle.evenodd import EvenOddOperator
+    wl = W.WORKLOADS[WL]
+    f = wl.fields[0]
+    tab = W.kappa_table()[f.name]
+    kappa = tab["kappa"]
+    u = f.gauge()
+    op = WilsonOperator(f.dims, u, kappa)
+    eo = EvenOddOperator(op)
+    eta = wl.sources_for(0)
+    s = seedcg.Solver(f.dims, u, kappa, precision="mixed_vbf16", past_factor=wl.past_factor,
+                      m_max=M_MAX, use_tensor_cores=1)
+    X = dev(np.zeros_like(eta))
+    code, info = seedcg.seedcg_solve_eo(s.h, dev(eta), X, wl.tol, 0, wl.reorth_period)
+    s.close()
+    torch.cuda.empty_cache()
+    assert code == seedcg.SEEDCG_OK
+    got = host(X)
+    lam_max = (1 + 8 * kappa) ** 4      # ||A^dag A|| <= (1 + kappa^2 ||H||^2)^2 <= (1 + 8 kappa)^4
+    worst = 0.0
+    for j in range(len(eta)):
+        b = eo.Adag(eo.source(eta[j])).reshape(-1)
+        xo = got[j][eo.odd].reshape(-1)
+        r = np.linalg.norm(b - eo.M(xo)) / np.linalg.norm(b)
+        assert r <= wl.tol + recompute_slack(lam_max, np.linalg.norm(xo), np.linalg.norm(b)), (j, r)
+        rd = np.linalg.norm(eta[j].reshape(-1) - op.D(got[j].reshape(-1))) / np.linalg.norm(eta[j])
+        assert abs(info["true_resid_D"][j] - rd) <= 1e-3 * rd + 1e-15, (j, rd, info["true_resid_D"][j])
+        worst = max(worst, r)
+    # the full-lattice run of the same sources converges RHS 1 at m_conv = 2064 (the
+    # headline test prints it); the even-odd system needs fewer Lanczos steps
+    assert info["m_conv"] < 2064, info["m_conv"]
+    print(f"even-odd 16^3x32 bf16: m_conv {info['m_conv']} m {info['m']} cg max {max(info['iters'][1:])} "
+          f"worst oracle residual {worst:.3e}, D residuals max {max(info['true_resid_D']):.2e}")
