@@ -66,3 +66,44 @@ def test_batch_rejects_mixed_precision_handles():
     assert e.value.code == seedcg.SEEDCG_ERR_ARG
     a.close()
     b.close()
+
+
+def test_uneven_workload_at_full_size_by_the_oracle():
+    """The three-field workload the bench's `batch3_uneven` line times
+    (8^3x16 / 12^3x24 / 16^3x32, 24 / 12 / 6 Z2 sources, FP32 iteration with a
+    complex64 basis and FP64 reliable updates, k = 10) in one seedcg_batch_solve:
+    all 42 residuals ||b - M x|| / ||b|| recomputed with the oracle's plain-C
+    FP64 operator meet tol, up to the rounding of a recomputation in another
+    summation order."""
+    need_gpu()
+    import torch
+    from tests.gpu_helpers import recompute_slack
+    wl = W.WORKLOADS["batch3_uneven_nrhs24_12_6"]
+    solvers, Bs, Xs, ops, lams = [], [], [], [], []
+    for i, f in enumerate(wl.fields):
+        u = f.gauge()
+        kappa = W.kappa_for(f.name)
+        op = WilsonOperator(f.dims, u, kappa)
+        eta = wl.sources_for(i)
+        B = np.stack([op.Ddag(e) for e in eta])      # the oracle's right-hand sides
+        s = seedcg.Solver(f.dims, u, kappa, precision=wl.precision, past_factor=wl.past_factor,
+                          m_max=4000)
+        solvers.append(s)
+        Bs.append(dev(B))
+        Xs.append(dev(np.zeros_like(B)))
+        ops.append(op)
+        lams.append(W.kappa_table().get(f.name, {}).get("lam_max", (1 + 8 * kappa) ** 2))
+    code, infos = seedcg.seedcg_batch_solve([s.h for s in solvers], Bs, Xs, wl.tol, 0, wl.reorth_period)
+    assert code == seedcg.SEEDCG_OK
+    worst = 0.0
+    for s, B, X, op, lam, info in zip(solvers, Bs, Xs, ops, lams, infos):
+        Bh, Xh = host(B), host(X)
+        for j in range(Bh.shape[0]):
+            b, x = Bh[j].reshape(-1), Xh[j].reshape(-1)
+            r = np.linalg.norm(b - op.M(x)) / np.linalg.norm(b)
+            assert r <= wl.tol + recompute_slack(lam, np.linalg.norm(x), np.linalg.norm(b)), (j, r)
+            worst = max(worst, r)
+        s.close()
+    torch.cuda.empty_cache()
+    print(f"three uneven fields, 42 systems: worst oracle residual {worst:.3e}; "
+          f"m_conv {[i['m_conv'] for i in infos]}, CG max {[i['cg_iters_max'] for i in infos]}")
