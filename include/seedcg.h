@@ -175,7 +175,10 @@ seedcg_status seedcg_batch_solve(seedcg_handle** hs, int nfields, const int* nrh
 
 /*
  * Apply the operator to n spinor fields (for parity checks and for forming
- * b = D^dag eta).  op: 0 = D, 1 = D^dag, 2 = M = D^dag D.  prec: 0 = FP64
+ * b = D^dag eta): the Wilson operator of Section 3, D = 1 - kappa H with the
+ * projector, gamma-basis and boundary conventions stated at the top of this
+ * header, D^dag = g5 D g5, and M = D^dag D, the matrix Algorithm 1 and the CG
+ * of Section 2 solve with.  op: 0 = D, 1 = D^dag, 2 = M = D^dag D.  prec: 0 = FP64
  * arithmetic, 1 = FP32 arithmetic (inputs rounded to FP32, result widened).
  * in/out: device pointers, complex128 [n][V][4][3]; they may not overlap.
  * multi = 1 uses the multi-RHS kernel (links staged once per site tile for
@@ -316,7 +319,11 @@ seedcg_status seedcg_guess_get_weights(seedcg_handle* h, double* w);
 seedcg_status seedcg_guess_loss_grad(seedcg_handle* h, int npairs, const double* B, const double* X,
                                      double* loss, double* grad, void* stream);
 /* Adam (beta = 0.9, 0.999, eps = 1e-8) over `epochs` passes of the pairs in
-   their given order, mini-batches of `batch`; *final_loss = last epoch's mean */
+   their given order, mini-batches of `batch`; *final_loss = last epoch's mean.
+   There is no random-number seed: training draws nothing at random (the weights
+   come from seedcg_guess_set_weights, the order of the pairs from the caller),
+   so a run is reproducible from its inputs alone; `stream` orders the work as in
+   seedcg_solve. */
 seedcg_status seedcg_guess_train(seedcg_handle* h, int npairs, const double* B, const double* X,
                                  int epochs, int batch, double lr, double* final_loss, void* stream);
 /* X0[k] = net(B[k]) */
