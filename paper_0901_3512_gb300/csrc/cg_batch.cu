@@ -560,12 +560,15 @@ k_mf_ru_resid(const int* __restrict__ row_of, const int* __restrict__ slot,
     }
     double red[1] = {part};
     rowsum<1>(red, partials, counters, [&](double* tot) {
-        const double rn = tot[0];
+        const double rn = tot[0], bn = C.bn[row];
         C.rr[row] = rn;
         C.rr_ru[row] = rn;
         C.flag[row] = 0;
-        tr_out[k] = C.bn[row] > 0.0 ? sqrt(rn) / C.bn[row] : 0.0;
-        C.active[row] = (C.bn[row] > 0.0 && sqrt(rn) > C.tol * C.bn[row]) ? 1 : 0;
+        // a non-finite b or residual is reported as such (never as converged) and the
+        // system leaves the iteration: the caller sees it as not converged
+        const bool finite = isfinite(rn) && isfinite(bn);
+        tr_out[k] = !finite ? rn + bn : bn > 0.0 ? sqrt(rn) / bn : 0.0;
+        C.active[row] = (finite && bn > 0.0 && sqrt(rn) > C.tol * bn) ? 1 : 0;
     });
 }
 
