@@ -3,6 +3,10 @@
 //   gemm_n:  Y += A C      (the Gram-Schmidt subtraction, X = X_0 + V Y)
 // Vectors are flat arrays of complex entries in the internal order; inner
 // products do not depend on that order.
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "reduce.cuh"
 
@@ -137,6 +141,98 @@ k_gemm_n(const AT* __restrict__ A, long lda, int na, const double2* __restrict__
                     size_t idx = (size_t)(b0 + c) * ldy + e;
                     cx_t<double> y = ld_cx<double>(Y, idx);
                     st_cx(Y, idx, make_double2(y.x + (double)acc[c].x, y.y + (double)acc[c].y));
+                }
+            }
+        }
+    }
+}
+
+// Two consecutive complex entries of a basis row in one load (8 bytes of bf16x2,
+// 16 of complex64), widened to cx_t<R>; FP64 rows take one entry per load.
+template <typename R, typename AT> struct Row2;
+template <typename R> struct Row2<R, __nv_bfloat162> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void get(const __nv_bfloat162* p, cx_t<R> (&o)[2]) {
+        const uint2 z = __ldcs(reinterpret_cast<const uint2*>(p));
+        __nv_bfloat162 b0, b1;
+        memcpy(&b0, &z.x, 4);
+        memcpy(&b1, &z.y, 4);
+        const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+        o[0] = mk<R>((R)f0.x, (R)f0.y);
+        o[1] = mk<R>((R)f1.x, (R)f1.y);
+    }
+};
+template <typename R> struct Row2<R, float2> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void get(const float2* p, cx_t<R> (&o)[2]) {
+        const float4 z = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = mk<R>((R)z.x, (R)z.y);
+        o[1] = mk<R>((R)z.z, (R)z.w);
+    }
+};
+template <typename R> struct Row2<R, double2> {
+    static constexpr int W = 1;
+    __device__ __forceinline__ static void get(const double2* p, cx_t<R> (&o)[1]) {
+        const double2 z = __ldcs(p);
+        o[0] = mk<R>((R)z.x, (R)z.y);
+    }
+};
+
+// Y[:, b0 .. b0+NB) += A C[:, b0 ..] for up to NB = 12 columns in ONE pass over the rows
+// of A (the seeds X += V Y of Eq. (1) read the stored basis once): a thread owns W
+// consecutive entries (one 8- or 16-byte load per row), the coefficients of CH rows
+// at a time sit in shared memory; Y is FP64 (double2).  n and lda are multiples of W.
+template <typename R, typename AT, int NB>
+__global__ void __launch_bounds__(256)
+k_gemm_n_wide(const AT* __restrict__ A, long lda, int na, const double2* __restrict__ C, int ldc,
+              int nb, int b0, double2* __restrict__ Y, long ldy, long n, double sign) {
+    constexpr int CH = 64;
+    constexpr int W = Row2<R, AT>::W;
+    __shared__ cx_t<R> sc[CH][NB];
+    const long ng = n / W;
+    for (long base = blockIdx.x * (long)blockDim.x; base < ng; base += (long)gridDim.x * blockDim.x) {
+        const long g = base + threadIdx.x;
+        cx_t<R> acc[W][NB];
+#pragma unroll
+        for (int w = 0; w < W; w++)
+#pragma unroll
+            for (int c = 0; c < NB; c++) acc[w][c] = mk<R>(0, 0);
+        for (int a0 = 0; a0 < na; a0 += CH) {
+            const int cnt = na - a0 < CH ? na - a0 : CH;
+            __syncthreads();
+            for (int k = threadIdx.x; k < CH * NB; k += blockDim.x) {
+                const int a = k / NB, c = k % NB;
+                const double2 z = (a < cnt && b0 + c < nb) ? C[(size_t)(a0 + a) * ldc + b0 + c]
+                                                           : make_double2(0.0, 0.0);
+                sc[a][c] = mk<R>((R)(sign * z.x), (R)(sign * z.y));
+            }
+            __syncthreads();
+            if (g < ng) {
+#pragma unroll 4
+                for (int a = 0; a < cnt; a++) {
+                    cx_t<R> av[W];
+                    Row2<R, AT>::get(A + (size_t)(a0 + a) * lda + g * W, av);
+#pragma unroll
+                    for (int c = 0; c < NB; c++) {
+                        const cx_t<R> cc = sc[a][c];
+#pragma unroll
+                        for (int w = 0; w < W; w++) acc[w][c] = cfma(av[w], cc, acc[w][c]);
+                    }
+                }
+            }
+        }
+        if (g < ng) {
+#pragma unroll
+            for (int c = 0; c < NB; c++) {
+                if (b0 + c < nb) {
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        const size_t idx = (size_t)(b0 + c) * ldy + g * W + w;
+                        double2 y = Y[idx];
+                        y.x += (double)acc[w][c].x;
+                        y.y += (double)acc[w][c].y;
+                        Y[idx] = y;
+                    }
                 }
             }
         }
@@ -375,6 +471,18 @@ void gemm_n(const AT* A, long lda, int na, const double2* C, int ldc, int nb, YT
         k_gemm_n<R, AT, YT, 2><<<blocks, 256, 0, s>>>(A, lda, na, C, ldc, nb, 0, Y, ldy, n, sign);
         SEEDCG_CHECK_LAUNCH();
         return;
+    }
+    constexpr int W = Row2<R, AT>::W;
+    if constexpr (std::is_same<YT, double2>::value) {
+        if (n % W == 0 && lda % W == 0 && (reinterpret_cast<uintptr_t>(A) & (W * sizeof(AT) - 1)) == 0) {
+            // one pass over A per 12 columns (the 11 seeds of the twelve-source workload)
+            const int wblocks = nblocks(n / W, 256, 152 * 8);
+            for (int b0 = 0; b0 < nb; b0 += 12) {
+                k_gemm_n_wide<R, AT, 12><<<wblocks, 256, 0, s>>>(A, lda, na, C, ldc, nb, b0, Y, ldy, n, sign);
+                SEEDCG_CHECK_LAUNCH();
+            }
+            return;
+        }
     }
     for (int b0 = 0; b0 < nb; b0 += 8) {
         k_gemm_n<R, AT, YT, 8><<<blocks, 256, 0, s>>>(A, lda, na, C, ldc, nb, b0, Y, ldy, n, sign);

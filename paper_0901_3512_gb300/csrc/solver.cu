@@ -625,31 +625,83 @@ k_norm2(const T* __restrict__ x, long n, double* partials, unsigned* ctr, double
 // phase S: Z = L^{-1} C, Y = U^{-1} Z column by column (Eq. 2 factors), in place
 // on C [m][ldc] double2.  One thread per right-hand side.
 // ===========================================================================
-__global__ void k_seed_tridiag(double2* C, int ldc, int nrhs, int m, LzDev L) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nrhs || m <= 0) return;
+// The two triangular solves are sequential in i; a block takes 32 right-hand sides
+// and walks the rows in chunks of SEED_CH: all threads stage a chunk of C and of the
+// scalars in shared memory (coalesced), one warp runs the recurrences on it (lane =
+// right-hand side), all threads write the chunk back.  Each step then waits on
+// shared memory instead of a global load.
+constexpr int SEED_CH = 64;
+__global__ void __launch_bounds__(256) k_seed_tridiag(double2* C, int ldc, int nrhs, int m, LzDev L) {
+    __shared__ double2 sc[SEED_CH][33];       // [row][rhs], padded against bank conflicts
+    __shared__ double sg[SEED_CH], sd[SEED_CH], sb[SEED_CH];   // gamma_{i-1}, 1 / delta_i, beta_i
+    const int j0 = blockIdx.x * 32;
+    const int nj = nrhs - j0 < 32 ? nrhs - j0 : 32;
+    if (nj <= 0 || m <= 0) return;
+    const int lane = threadIdx.x & 31;
+    const bool runner = threadIdx.x < 32 && lane < nj;
+    auto load_chunk = [&](int i0, int cnt) {
+        for (int k = threadIdx.x; k < cnt * 32; k += blockDim.x) {
+            const int r = k / 32, c = k % 32;
+            if (c < nj) sc[r][c] = C[(size_t)(i0 + r) * ldc + j0 + c];
+        }
+        for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+            const int i = i0 + r + 1;                  // 1-based row
+            sg[r] = i >= 2 ? L.gamma[i - 2] : 0.0;     // gamma_{i-1}
+            sd[r] = 1.0 / L.delta[i - 1];              // the chain then multiplies
+            sb[r] = i <= m - 1 ? L.beta[i - 1] : 0.0;  // beta_i couples rows i and i+1
+        }
+    };
+    auto store_chunk = [&](int i0, int cnt) {
+        for (int k = threadIdx.x; k < cnt * 32; k += blockDim.x) {
+            const int r = k / 32, c = k % 32;
+            if (c < nj) C[(size_t)(i0 + r) * ldc + j0 + c] = sc[r][c];
+        }
+    };
     // forward: eta_1 = c_1, eta_i = c_i - gamma_{i-1} eta_{i-1}
-    double2 prev = C[j];
-    for (int i = 2; i <= m; i++) {
-        double gm = L.gamma[i - 2];
-        double2 c = C[(size_t)(i - 1) * ldc + j];
-        c.x -= gm * prev.x;
-        c.y -= gm * prev.y;
-        C[(size_t)(i - 1) * ldc + j] = c;
-        prev = c;
+    double2 prev = make_double2(0.0, 0.0);
+    for (int i0 = 0; i0 < m; i0 += SEED_CH) {
+        const int cnt = m - i0 < SEED_CH ? m - i0 : SEED_CH;
+        __syncthreads();
+        load_chunk(i0, cnt);
+        __syncthreads();
+        if (runner) {
+            for (int r = 0; r < cnt; r++) {
+                double2 c = sc[r][lane];
+                if (i0 + r > 0) {
+                    c.x -= sg[r] * prev.x;
+                    c.y -= sg[r] * prev.y;
+                }
+                sc[r][lane] = c;
+                prev = c;
+            }
+        }
+        __syncthreads();
+        store_chunk(i0, cnt);
     }
-    // back substitution with U (delta on, beta above the diagonal)
-    double2 y = C[(size_t)(m - 1) * ldc + j];
-    y.x /= L.delta[m - 1];
-    y.y /= L.delta[m - 1];
-    C[(size_t)(m - 1) * ldc + j] = y;
-    for (int i = m - 1; i >= 1; i--) {
-        double2 z = C[(size_t)(i - 1) * ldc + j];
-        double b = L.beta[i - 1];
-        z.x = (z.x - b * y.x) / L.delta[i - 1];
-        z.y = (z.y - b * y.y) / L.delta[i - 1];
-        C[(size_t)(i - 1) * ldc + j] = z;
-        y = z;
+    // back substitution with U (delta on the diagonal, beta above it):
+    // y_m = z_m / delta_m, y_i = (z_i - beta_i y_{i+1}) / delta_i
+    double2 y = make_double2(0.0, 0.0);
+    for (int iend = m; iend > 0; iend -= SEED_CH) {
+        const int i0 = iend - SEED_CH > 0 ? iend - SEED_CH : 0;
+        const int cnt = iend - i0;
+        __syncthreads();
+        load_chunk(i0, cnt);
+        __syncthreads();
+        if (runner) {
+            for (int r = cnt - 1; r >= 0; r--) {
+                double2 z = sc[r][lane];
+                if (i0 + r < m - 1) {
+                    z.x -= sb[r] * y.x;
+                    z.y -= sb[r] * y.y;
+                }
+                z.x *= sd[r];
+                z.y *= sd[r];
+                sc[r][lane] = z;
+                y = z;
+            }
+        }
+        __syncthreads();
+        store_chunk(i0, cnt);
     }
 }
 
@@ -1035,7 +1087,7 @@ seedcg_status run_solve(seedcg_handle* h, int nrhs, const double2* B64, double2*
     const int ns = nrhs - 1;
     if (!literal && m > 0 && ns > 0) {
         project(m, R0 + n, ns, ns);
-        k_seed_tridiag<<<(ns + 63) / 64, 64, 0, st>>>(Cc, ns, ns, m, L);
+        k_seed_tridiag<<<(ns + 31) / 32, 256, 0, st>>>(Cc, ns, ns, m, L);
         SEEDCG_CHECK_LAUNCH();
         gemm_n<R, VT, double2>(Vb, n, m, Cc, ns, ns, X64 + n, n, n, 1.0, st);
     }
