@@ -362,10 +362,20 @@ k_mf_brick(const GroupDev<R>* __restrict__ G, Rows rows, CgS C) {
     }
 }
 
-// a row's shares, summed in a fixed order (one block per row)
+// a row's shares, summed in a fixed order (one block per row); four independent
+// partial sums per thread keep four loads in flight
 __device__ __forceinline__ double row_shares(const double* __restrict__ sh, int ntiles) {
-    double v[1] = {0.0};
-    for (int b = threadIdx.x; b < ntiles; b += blockDim.x) v[0] += sh[b];
+    const int bd = blockDim.x;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int b = threadIdx.x;
+    for (; b + 3 * bd < ntiles; b += 4 * bd) {
+        v0 += sh[b];
+        v1 += sh[b + bd];
+        v2 += sh[b + 2 * bd];
+        v3 += sh[b + 3 * bd];
+    }
+    for (; b < ntiles; b += bd) v0 += sh[b];
+    double v[1] = {(v0 + v1) + (v2 + v3)};
     block_sum<1>(v);
     return v[0];
 }
