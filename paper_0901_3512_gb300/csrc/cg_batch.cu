@@ -1,7 +1,8 @@
 // Batched CG engine (the "standard CG" of Section 2 for every seeded system,
 // run for all systems of all gauge fields at once).
 //
-// Every iteration is five launches whatever the number of fields or systems:
+// Every iteration is five launches whatever the number of fields or systems (seven
+// for the even-odd system, whose operator is four parity-restricted hops):
 //   1. one multi-field multi-RHS dslash  t = D p   (tiles of 32 sites of every
 //      field; each tile stages its links once, scaled by -kappa and the
 //      boundary sign, and applies them to all of the field's active systems),

@@ -23,7 +23,8 @@ struct CgResult {
     std::vector<std::vector<double>> true_resid;
     int reliable_updates = 0;
     int graph_chunks = 0;
-    int rpb = 0;          // warps per dslash tile chosen by the autotuner
+    int rpb = 0;          // the operator's launch shape chosen by the autotuner (warps per
+                          // 32-site tile, or TB * 1000 + groups for the brick kernel)
 };
 
 // Run CG on every system of every group until ||b - M x|| <= tol ||b|| in FP64.
